@@ -1,0 +1,366 @@
+"""Benchmark of the on-line back projection (Eq. (BP)) on the paper-shaped frame.
+
+Workload (the paper's 0.39 mm case, Sec. III): 256x256 grid at 0.1 mm, skull
+ring 2200-3000 m/s, 512 sensors on a ring, 2048 FP32 samples, 21 323
+reconstructed pixels; synthetic signals (see paper_1501_03869_gb300/synth.py).
+One step = one frame through the whole on-line path: the preprocessing kernel
+(b = 2p - 2t dp/dt) and the gather kernel.  The table (off-line fast marching)
+is built before timing, as in the paper.
+
+Output: one JSON line (rank 0).  `value` is pixel*sensor updates per second
+(G/s) of the single-frame FP32 path with inputs resident in HBM, L2 flushed
+before every step; `e2e` is the same metric through pat_bp_reconstruct_host
+(pinned host buffers, copies inside the timed region); `forms` adds the
+batched FP32 / BF16 forms; `cpu_baseline` is the FP64 oracle on this host.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G pixel·sensor updates/s & frames/s; p50/p99 frame latency vs plain FP32 kernel"
+UNIT = "G pixel*sensor updates/s"
+WORKLOAD = ("paper-shaped frame: 2D 256x256 dx 0.1 mm, skull ring 2200-3000 m/s, 512 sensors "
+            "on a ring, 2048 FP32 samples, 21323-pixel disc mask, plain FP32 kernel")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch-frames", type=int, default=64)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("kernels.cu", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1501_03869_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(per_update_units):
+    """DRAM bytes per launch of the gather kernel from the committed ncu summary,
+    scaled to this launch; None if the kernel changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "gather_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("kernel_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_update"]) * per_update_units
+
+
+def oracle_cpu_rate(w, n_sensors, seconds, frames=1):
+    """FP64 oracle back projection on this host: updates/s over a bounded run."""
+    import oracle
+    pix = np.flatnonzero(w.mask.ravel())
+    sens = w.sensors[:n_sensors]
+    T = oracle.travel_table(w.speed, w.dx, w.origin, sens, pix)
+    p = w.signals[0, :n_sensors].astype(np.float64)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.bp(T, p, w.dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return n * n_sensors * pix.size / el, el, n
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    from paper_1501_03869_gb300 import synth
+    import oracle
+    w = synth.config2(n_frames=1)
+    pix = np.flatnonzero(w.mask.ravel())
+    T = oracle.travel_table(w.speed, w.dx, w.origin, w.sensors, pix)
+    p = w.signals[0].astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.bp(T, p, w.dt)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.bp(T, p, w.dt)
+        times.append(time.perf_counter() - t0)
+    upd = w.n_sensors * pix.size
+    tot = sum(times)
+    val = upd * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "frames_per_s": args.steps / tot,
+        "config": {"workload": WORKLOAD, "global_batch": 1, "n_sensors": w.n_sensors,
+                   "n_pix": int(pix.size), "n_samples": w.nt, "l2": "host run"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "full 512-sensor frame per step, FP64 oracle back projection "
+                                   "(table built before timing)"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(fn, steps, warmup, stream, flush):
+    """Per-step device times (ms) of fn(); L2 flushed before every step, events
+    on `stream`.  fn returns a list of (name, start_evt, end_evt) spans."""
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    recs = []
+    for _ in range(steps):
+        flush.zero_()
+        recs.append(fn())
+    torch.cuda.synchronize()
+    return recs
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1501_03869_gb300 import BP, synth
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    w = synth.config2(n_frames=1)
+    bp = BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask)
+    info = bp.info
+    n_pix, ns, nt = info["n_pix"], w.n_sensors, w.nt
+    updates = n_pix * ns
+    sig = torch.from_numpy(w.signals).to(dev)
+    out = torch.empty(bp.out_shape(1), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    bp.reserve(max(args.batch_frames, 1))
+    Ev = torch.cuda.Event
+
+    def step():
+        e0, e1, e2 = Ev(enable_timing=True), Ev(enable_timing=True), Ev(enable_timing=True)
+        e0.record(stream)
+        bp.preprocess(sig, stream=stream)
+        e1.record(stream)
+        bp.gather(1, out, stream=stream)
+        e2.record(stream)
+        return e0, e1, e2
+
+    # ---------------------------------------------------- timed single frame --
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local_rank) as clk:
+        recs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            recs.append(step())
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    bp.sync()
+    step_ms = [a.elapsed_time(c) for a, b, c in recs]
+    pre_ms = [a.elapsed_time(b) for a, b, c in recs]
+    gat_ms = [b.elapsed_time(c) for a, b, c in recs]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * updates * args.steps / (tot_ms / 1e3) / 1e9
+    clocks = clk.summary()
+
+    # ------------------------------------------------------------ roofline --
+    hbm_peak, peak_kind = peaks()
+    alg_bytes = 4.0 * ns * n_pix + 4.0 * ns * nt + 4.0 * n_pix
+    gat_avg_s = statistics.mean(gat_ms) / 1e3
+    achieved = alg_bytes / gat_avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": peak_kind,
+                "traffic": ncu_traffic(updates), "kernel": "gather_kernel<128,1,f32>",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "gather_us": statistics.mean(gat_ms) * 1e3,
+                "preprocess_us": statistics.mean(pre_ms) * 1e3}
+
+    # ------------------------------------------------------------------ e2e --
+    pin_sig = torch.empty(w.signals.shape, dtype=torch.float32, pin_memory=True)
+    pin_sig.copy_(torch.from_numpy(w.signals))
+    pin_out = torch.empty(bp.out_shape(1), dtype=torch.float32, pin_memory=True)
+    sig_np, out_np = pin_sig.numpy(), pin_out.numpy()
+    for _ in range(args.warmup):
+        bp.reconstruct_host(sig_np, out=out_np)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bp.reconstruct_host(sig_np, out=out_np)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": world * updates * args.steps / sum(e2e_t) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(w.signals.nbytes), "d2h_bytes_per_step": int(out_np.nbytes),
+           "ms_per_step": sum(e2e_t) / args.steps * 1e3,
+           "p50_ms": float(np.percentile(e2e_t, 50) * 1e3),
+           "p99_ms": float(np.percentile(e2e_t, 99) * 1e3)}
+
+    # --------------------------------------------------------------- forms --
+    forms = {}
+    if not args.no_forms and args.batch_frames > 1:
+        F = args.batch_frames
+        rng = np.random.default_rng(7)
+        sigF = torch.from_numpy(
+            (w.signals[0][None] * rng.uniform(0.5, 1.5, (F, 1, 1))).astype(np.float32)).to(dev)
+        outF = torch.empty(bp.out_shape(F), device=dev)
+        codes, sc, _ = synth.quantise(sigF.cpu().numpy(), "bf16")
+        sig16 = torch.from_numpy(codes.astype(np.int16)).to(dev).view(torch.bfloat16)
+        sc16 = torch.from_numpy(sc).to(dev)
+        for name, s, scl in (("batched_f32", sigF, None), ("batched_bf16", sig16, sc16)):
+            def fstep(s=s, scl=scl):
+                e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
+                e0.record(stream)
+                bp.reconstruct(s, scales=scl, out=outF, stream=stream)
+                e1.record(stream)
+                return e0, e1
+            n_rep = max(3, args.steps // 5)
+            rr = time_steps(fstep, n_rep, 2, stream, flush)
+            ms = statistics.mean(a.elapsed_time(b) for a, b in rr)
+            forms[name] = {"frames": F, "ms_per_batch": ms, "frames_per_s": F / (ms / 1e3),
+                           "value": F * updates / (ms / 1e3) / 1e9, "unit": UNIT}
+        bp.sync()
+
+    # -------------------------------------------------------- cpu baseline --
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n_s = 128
+        rate, el, n = oracle_cpu_rate(w, n_s, args.cpu_seconds)
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} runs of the FP64 oracle back projection over the first {n_s} "
+                         f"sensors x {n_pix} pixels ({el:.1f} s, table built before timing)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "frames_per_s": world * args.steps / (tot_ms / 1e3),
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "config": {"workload": WORKLOAD, "global_batch": world, "n_sensors": ns,
+                       "n_pix": n_pix, "n_samples": nt, "tile_pix": info["tile_pix"],
+                       "split": info["split"], "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every step (512 MB write)"},
+            "gpu_launches": 2 * args.steps, "roofline": roofline, "e2e": e2e, "forms": forms,
+            "clocks": clocks, "cpu_baseline": cpu, "wall_s": wall,
+            "paper_context": {"ms": 123.79, "hardware": "Tesla C2075, incl. transfers",
+                              "note": "sample count not stated in the paper"},
+        }
+        print(json.dumps(line), flush=True)
+    bp.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * pat_bp.h -- C ABI of the GB300 fast-marching back-projection library.
+ *
+ * Method (Wang & Jing, "A fast marching method based back projection algorithm
+ * for photoacoustic tomography in heterogeneous media"):
+ *   - Sec. II-B: travel times T_s(r) from every sensor s to every pixel r solve
+ *     the eikonal equation |grad T|^2 = 1/c^2 by fast marching, run once per
+ *     speed map with the sensor as the point source (ray paths are reversible).
+ *   - Sec. II-C, Eq. (BP): every pixel sums over the sensors the integrand
+ *     b_s(t) = 2 p_s(t) - 2 t dp_s/dt sampled at t = T_s(r), weighted by w_s.
+ *   - Sec. III: the travel-time table is computed off line once; the per-frame
+ *     ("on-line") work is the back projection only.
+ *
+ * Conventions shared by every entry point:
+ *   - No exception crosses the ABI; every call returns a pat_status.  CUDA
+ *     errors map to PAT_ERR_CUDA; a device-side wait that ran out of time maps
+ *     to PAT_ERR_TIMEOUT when the status is read (pat_bp_sync).
+ *   - "host" pointers are ordinary CPU memory, "dev" pointers are device
+ *     memory of the current CUDA device.  The library copies every host input
+ *     it keeps; it never frees caller memory.
+ *   - Grid nodes: node (i, j, k) sits at origin + (i, j, k) * dx (metres), x
+ *     fastest in every array; 2-D grids use n[2] = 1.
+ *   - Signals are [F][N_s][N_t] row-major; sample k of every row is at t = k dt
+ *     (t = 0 is the laser pulse, the initial condition of Sec. II-A).
+ */
+#ifndef PAT_BP_H
+#define PAT_BP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PAT_OK = 0,
+  PAT_ERR_INVALID = 1,   /* bad argument (sizes, pointers, geometry)          */
+  PAT_ERR_OOM = 2,       /* device or host allocation failed                 */
+  PAT_ERR_CUDA = 3,      /* a CUDA runtime call failed                       */
+  PAT_ERR_TIMEOUT = 4,   /* a bounded device or host wait ran out            */
+  PAT_ERR_BUSY = 5,      /* admission refused for now (serving)              */
+  PAT_ERR_NOT_FOUND = 6, /* unknown ticket / subject (serving)               */
+  PAT_PENDING = 7        /* request still in flight (serving)                */
+} pat_status;
+
+typedef enum { PAT_F32 = 0, PAT_BF16 = 1, PAT_F16 = 2 } pat_dtype;
+
+typedef struct {
+  int ndim;          /* 2 or 3                                               */
+  int n[3];          /* nodes along x, y, z (n[2] = 1 when ndim == 2)         */
+  double dx;         /* node spacing (m), > 0                                 */
+  double origin[3];  /* position of node (0,0,0) (m)                          */
+} pat_grid;
+
+typedef struct pat_bp_s* pat_bp_t;
+typedef void* pat_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+/* Flags of pat_bp_create. */
+#define PAT_FLAG_COMPACT_OUT 0x1u /* out is [F][N_pix] in raster order of the mask
+                                     instead of the dense [F][grid] image        */
+#define PAT_FLAG_TILE_128 0x10u   /* force 128 pixels per tile                   */
+#define PAT_FLAG_TILE_256 0x20u   /* force 256 pixels per tile                   */
+
+/* Read-only facts about a handle (pat_bp_info). */
+typedef struct {
+  int64_t n_pix;        /* reconstructed (mask) pixels                        */
+  int64_t grid_total;   /* nodes of the dense grid                            */
+  int n_sensors, n_samples, n_samples_pad;
+  int tile_pix;         /* P: pixels per tile                                 */
+  int n_tiles;
+  int window;           /* W: samples of one sensor a tile can touch          */
+  int split;            /* sensor splits per tile (thread-block cluster size) */
+  int sensor_warps;     /* warps that share a tile's sensors inside one CTA   */
+  int64_t table_bytes;  /* device bytes of the travel-time table              */
+  double build_seconds; /* host time of the fast-marching table build         */
+} pat_bp_info_t;
+
+const char* pat_status_str(pat_status s);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* pat_last_error(void);
+
+/* pat_bp_create -- the off-line step of Sec. III: fast-marching travel times
+ * (Sec. II-B, first-order Godunov upwind update, one FP64 run per sensor on
+ * the host, all host cores), stored on the device as FP32 sample offsets
+ * u = T/dt - base from an int32 base per (pixel tile, sensor).
+ *   speed_host    [n_z][n_y][n_x] sound speed (m/s) at the nodes, all > 0
+ *   grid          geometry of speed_host (and of the dense output)
+ *   sensors_host  [n_sensors][3] positions (m); each inside the grid box
+ *   mask_host     [grid] nonzero = reconstruct that pixel; NULL = all nodes
+ *   weights_host  [n_sensors] w_s of Eq. (BP); NULL = 1/n_sensors each
+ *   dt, n_samples sample interval (s, > 0) and samples per signal (2..65536)
+ *   flags         PAT_FLAG_* (0 = defaults)
+ *   out           receives the handle (owns all device memory it allocates)
+ * Uses the current CUDA device.  Blocking.  Errors: PAT_ERR_INVALID for bad
+ * geometry, PAT_ERR_OOM, PAT_ERR_CUDA. */
+pat_status pat_bp_create(const float* speed_host, const pat_grid* grid,
+                         const double* sensors_host, int n_sensors,
+                         const uint8_t* mask_host, const float* weights_host,
+                         double dt, int n_samples, unsigned flags, pat_bp_t* out);
+
+/* pat_bp_reconstruct -- the on-line step: Eq. (BP) for n_frames frames that
+ * share the handle's table.
+ *   signals_dev   [n_frames][n_sensors][n_samples] of dtype; for PAT_BF16 and
+ *                 PAT_F16 the pressure is code * scale
+ *   scales_dev    [n_frames][n_sensors] FP32 per-row scales; required for the
+ *                 16-bit dtypes, optional (NULL = 1) for PAT_F32
+ *   out_dev       [n_frames][grid] dense image (zeros outside the mask), or
+ *                 [n_frames][n_pix] with PAT_FLAG_COMPACT_OUT
+ *   stream        CUDA stream; the call is asynchronous on it
+ * FP32 signals are preprocessed into FP32 integrands; 16-bit signals into
+ * 16-bit (value, slope) pairs with a per-row FP32 scale.  Accumulation is FP32.
+ * The first call with more frames than any earlier call grows the handle's
+ * integrand buffer (a device allocation); pat_bp_reserve avoids that.
+ * Calls on one handle must not overlap on the GPU (they share that buffer).
+ * The caller keeps signals/out alive until the stream passes this point. */
+pat_status pat_bp_reconstruct(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                              const float* scales_dev, int n_frames, float* out_dev,
+                              pat_stream_t stream);
+
+/* pat_bp_preprocess / pat_bp_gather -- the two kernels of pat_bp_reconstruct
+ * as separate calls (same arguments, same buffers): pat_bp_preprocess forms
+ * the Eq. (BP) integrand of n_frames frames into the handle's buffer;
+ * pat_bp_gather back-projects the last preprocessed n_frames frames into
+ * out_dev.  pat_bp_reconstruct == preprocess then gather on one stream. */
+pat_status pat_bp_preprocess(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                             const float* scales_dev, int n_frames, pat_stream_t stream);
+pat_status pat_bp_gather(pat_bp_t h, int n_frames, float* out_dev, pat_stream_t stream);
+
+/* pat_bp_reconstruct_host -- the paper's timed on-line path (Sec. III): copy
+ * signals and scales from host memory, reconstruct, copy the image back.
+ * Synchronous; uses the handle's own stream and staging buffers.  Pinned host
+ * memory gives the fastest copies but is not required. */
+pat_status pat_bp_reconstruct_host(pat_bp_t h, const void* signals_host, pat_dtype dtype,
+                                   const float* scales_host, int n_frames, float* out_host);
+
+/* pat_bp_reserve -- allocate the integrand buffer for up to max_frames frames
+ * of dtype now, so later calls allocate nothing. */
+pat_status pat_bp_reserve(pat_bp_t h, int max_frames, pat_dtype dtype);
+
+/* pat_bp_sync -- wait for `stream`, then report a device-side timeout recorded
+ * by any earlier launch of this handle (and clear it). */
+pat_status pat_bp_sync(pat_bp_t h, pat_stream_t stream);
+
+/* pat_bp_info -- sizes and layout facts of the handle. */
+pat_status pat_bp_info(pat_bp_t h, pat_bp_info_t* info);
+
+/* pat_bp_table -- copy the device table back (tests): u_host [n_tiles][n_sensors]
+ * [tile_pix] FP32 offsets, base_host [n_tiles][n_sensors] int32 bases, pix_host
+ * [n_tiles * tile_pix] output index of each slot (-1 = padding).  Any pointer
+ * may be NULL.  u + base is T/dt; entries out of the record hold 1e30. */
+pat_status pat_bp_table(pat_bp_t h, float* u_host, int32_t* base_host, int32_t* pix_host);
+
+/* pat_bp_destroy -- free the handle and its device memory (synchronises). */
+pat_status pat_bp_destroy(pat_bp_t h);
+
+/* pat_fmm_host -- the library's own host fast marching (Sec. II-B) from one
+ * point source; T_out [grid] receives FP64 arrival times (s).  CPU only. */
+pat_status pat_fmm_host(const float* speed_host, const pat_grid* grid, const double* src_xyz,
+                        double* T_out);
+
+/* pat_table_host -- the table pat_bp_create would upload, built on the host
+ * only (no GPU needed): same arguments as pat_bp_create.  info receives the
+ * sizes; u_host [n_tiles][n_sensors][tile_pix], base_host [n_tiles][n_sensors]
+ * and slot_host [n_tiles * tile_pix] are filled when non-NULL (call once with
+ * NULL buffers to learn the sizes).  The split/sensor_warps fields of info
+ * are not set.  CPU only. */
+pat_status pat_table_host(const float* speed_host, const pat_grid* grid, const double* sensors_host,
+                          int n_sensors, const uint8_t* mask_host, double dt, int n_samples,
+                          unsigned flags, pat_bp_info_t* info, float* u_host, int32_t* base_host,
+                          int32_t* slot_host);
+
+/* pat_test_wait_timeout -- launches one CTA whose mbarrier wait can never
+ * complete, bounded by timeout_ns; returns PAT_ERR_TIMEOUT when the kernel
+ * gave up and reported it, PAT_OK if it (wrongly) completed.  Exercises the
+ * failure path of every bounded device wait without faulting the GPU. */
+pat_status pat_test_wait_timeout(uint64_t timeout_ns);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAT_BP_H */

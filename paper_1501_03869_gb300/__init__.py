@@ -1,0 +1,243 @@
+"""GB300 fast-marching back projection for photoacoustic tomography.
+
+Wang & Jing, "A fast marching method based back projection algorithm for
+photoacoustic tomography in heterogeneous media":
+  * Sec. II-B: fast-marching travel times from each sensor (off line, once per
+    speed map) -- built on the host inside :class:`BP` creation;
+  * Sec. II-C, Eq. (BP): per-frame back projection of 2p - 2t dp/dt at those
+    travel times -- CUDA kernels for sm_103a behind the C ABI of
+    ``include/pat_bp.h``.
+
+PyTorch is used for device memory and streams only.  The CUDA library is
+loaded lazily; any call fails loudly when it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import PatError
+
+__all__ = ["BP", "PatError", "fmm_host", "table_host", "wait_timeout_probe", "DTYPES"]
+
+DTYPES = {"f32": _lib.PAT_F32, "bf16": _lib.PAT_BF16, "f16": _lib.PAT_F16}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    m = {torch.float32: _lib.PAT_F32, torch.bfloat16: _lib.PAT_BF16, torch.float16: _lib.PAT_F16}
+    if t.dtype not in m:
+        raise TypeError(f"signals must be float32, bfloat16 or float16, not {t.dtype}")
+    return m[t.dtype]
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class BP:
+    """One speed map, sensor layout and mask with its device travel-time table.
+
+    speed      ([nz,] ny, nx) sound speed (m/s) at the nodes
+    dx         node spacing (m); origin: position of node 0 (x first, m)
+    sensors    [ns, 3] sensor positions (m)
+    dt, n_samples   sampling of every signal (t_k = k dt)
+    mask       grid-shaped, nonzero = reconstruct (None = all nodes)
+    weights    [ns] w_s of Eq. (BP) (None = 1/ns)
+    """
+
+    def __init__(self, speed, dx, origin, sensors, dt, n_samples, mask=None, weights=None,
+                 flags=0, compact=False):
+        lib = _lib.load()
+        speed = np.ascontiguousarray(speed, dtype=np.float32)
+        self.shape = speed.shape
+        self.grid = _lib.make_grid(speed.shape, dx, origin)
+        sensors = np.ascontiguousarray(sensors, dtype=np.float64)
+        if sensors.ndim != 2 or sensors.shape[1] != 3:
+            raise ValueError("sensors must be [ns, 3]")
+        self.n_sensors = sensors.shape[0]
+        self.n_samples = int(n_samples)
+        self.dt = float(dt)
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        if m is not None and m.shape != speed.shape:
+            raise ValueError("mask must have the grid's shape")
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        if compact:
+            flags |= _lib.PAT_FLAG_COMPACT_OUT
+        self.compact = bool(flags & _lib.PAT_FLAG_COMPACT_OUT)
+        h = ctypes.c_void_p()
+        _lib.check(lib.pat_bp_create(speed.ctypes.data, ctypes.byref(self.grid), sensors.ctypes.data,
+                                     self.n_sensors, None if m is None else m.ctypes.data,
+                                     None if w is None else w.ctypes.data, self.dt, self.n_samples,
+                                     flags, ctypes.byref(h)), "pat_bp_create")
+        self._h = h
+        self._lib = lib
+        inf = _lib.PatInfo()
+        _lib.check(lib.pat_bp_info(h, ctypes.byref(inf)), "pat_bp_info")
+        self.info = {k: getattr(inf, k) for k, _ in _lib.PatInfo._fields_}
+
+    # ------------------------------------------------------------ lifecycle --
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pat_bp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_pix(self):
+        return int(self.info["n_pix"])
+
+    def out_shape(self, n_frames):
+        return (n_frames, self.n_pix) if self.compact else (n_frames,) + tuple(self.shape)
+
+    # -------------------------------------------------------------- compute --
+    def reconstruct(self, signals, scales=None, out=None, stream=None):
+        """Eq. (BP) for signals [F, ns, nt] (CUDA tensor).  Asynchronous on
+        `stream` (default: torch's current stream).  Returns `out`."""
+        torch = _torch()
+        if signals.dim() == 2:
+            signals = signals.unsqueeze(0)
+        if not signals.is_cuda or not signals.is_contiguous():
+            raise ValueError("signals must be a contiguous CUDA tensor")
+        F, ns, nt = signals.shape
+        if ns != self.n_sensors or nt != self.n_samples:
+            raise ValueError(f"signals shape {tuple(signals.shape)} does not match the handle")
+        code = _dtype_code(signals)
+        if scales is not None:
+            if not scales.is_cuda or scales.dtype != torch.float32 or not scales.is_contiguous():
+                raise ValueError("scales must be a contiguous float32 CUDA tensor")
+            if tuple(scales.shape) != (F, ns):
+                raise ValueError("scales must be [F, ns]")
+        if out is None:
+            out = torch.empty(self.out_shape(F), dtype=torch.float32, device=signals.device)
+        elif not out.is_contiguous() or out.dtype != torch.float32 or out.numel() != int(
+                np.prod(self.out_shape(F))):
+            raise ValueError("out must be a contiguous float32 tensor of the output shape")
+        _lib.check(self._lib.pat_bp_reconstruct(
+            self._h, ctypes.c_void_p(signals.data_ptr()), code,
+            None if scales is None else ctypes.c_void_p(scales.data_ptr()), F,
+            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "pat_bp_reconstruct")
+        return out
+
+    def preprocess(self, signals, scales=None, stream=None):
+        """First kernel only: Eq. (BP) integrand of signals [F, ns, nt] into the
+        handle's buffer (asynchronous)."""
+        if signals.dim() == 2:
+            signals = signals.unsqueeze(0)
+        if not signals.is_cuda or not signals.is_contiguous():
+            raise ValueError("signals must be a contiguous CUDA tensor")
+        F = signals.shape[0]
+        _lib.check(self._lib.pat_bp_preprocess(
+            self._h, ctypes.c_void_p(signals.data_ptr()), _dtype_code(signals),
+            None if scales is None else ctypes.c_void_p(scales.data_ptr()), F,
+            _stream_ptr(stream)), "pat_bp_preprocess")
+        return F
+
+    def gather(self, n_frames, out, stream=None):
+        """Second kernel only: back projection of the last preprocessed frames."""
+        if not out.is_contiguous() or out.dtype != _torch().float32 or out.numel() != int(
+                np.prod(self.out_shape(n_frames))):
+            raise ValueError("out must be a contiguous float32 tensor of the output shape")
+        _lib.check(self._lib.pat_bp_gather(self._h, int(n_frames), ctypes.c_void_p(out.data_ptr()),
+                                           _stream_ptr(stream)), "pat_bp_gather")
+        return out
+
+    def reconstruct_host(self, signals, dtype="f32", scales=None, out=None):
+        """Host-to-host path: numpy signals [F, ns, nt] (float32, or uint16 codes
+        for 'bf16'/'f16' with float32 scales [F, ns]); returns the image."""
+        code = DTYPES[dtype]
+        sig = np.ascontiguousarray(signals)
+        if sig.ndim == 2:
+            sig = sig[None]
+        want = np.float32 if code == _lib.PAT_F32 else np.uint16
+        if sig.dtype != want:
+            raise TypeError(f"{dtype} signals must be {np.dtype(want).name}")
+        F = sig.shape[0]
+        sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+        if out is None:
+            out = np.empty(self.out_shape(F), dtype=np.float32)
+        _lib.check(self._lib.pat_bp_reconstruct_host(
+            self._h, sig.ctypes.data, code, None if sc is None else sc.ctypes.data, F,
+            out.ctypes.data), "pat_bp_reconstruct_host")
+        return out
+
+    def reserve(self, max_frames, dtype="f32"):
+        _lib.check(self._lib.pat_bp_reserve(self._h, int(max_frames), DTYPES[dtype]),
+                   "pat_bp_reserve")
+
+    def sync(self, stream=None):
+        _lib.check(self._lib.pat_bp_sync(self._h, _stream_ptr(stream)), "pat_bp_sync")
+
+    def table(self):
+        """(u [tiles, ns, P] float32, base [tiles, ns] int32, slot [tiles*P] int32)."""
+        nt, ns, P = self.info["n_tiles"], self.n_sensors, self.info["tile_pix"]
+        u = np.empty((nt, ns, P), dtype=np.float32)
+        b = np.empty((nt, ns), dtype=np.int32)
+        s = np.empty(nt * P, dtype=np.int32)
+        _lib.check(self._lib.pat_bp_table(self._h, u.ctypes.data, b.ctypes.data, s.ctypes.data),
+                   "pat_bp_table")
+        return u, b, s
+
+
+def fmm_host(speed, dx, origin, src):
+    """The library's host fast marching (FP64) from one point source."""
+    lib = _lib.load()
+    speed = np.ascontiguousarray(speed, dtype=np.float32)
+    g = _lib.make_grid(speed.shape, dx, origin)
+    src = np.ascontiguousarray(np.resize(np.asarray(src, dtype=np.float64), 3))
+    T = np.empty(speed.shape, dtype=np.float64)
+    _lib.check(lib.pat_fmm_host(speed.ctypes.data, ctypes.byref(g), src.ctypes.data, T.ctypes.data),
+               "pat_fmm_host")
+    return T
+
+
+def table_host(speed, dx, origin, sensors, dt, n_samples, mask=None, flags=0):
+    """The device table, built on the host only: (info, u, base, slot)."""
+    lib = _lib.load()
+    speed = np.ascontiguousarray(speed, dtype=np.float32)
+    g = _lib.make_grid(speed.shape, dx, origin)
+    sensors = np.ascontiguousarray(sensors, dtype=np.float64)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    inf = _lib.PatInfo()
+    args = (speed.ctypes.data, ctypes.byref(g), sensors.ctypes.data, sensors.shape[0],
+            None if m is None else m.ctypes.data, float(dt), int(n_samples), int(flags),
+            ctypes.byref(inf))
+    _lib.check(lib.pat_table_host(*args, None, None, None), "pat_table_host")
+    nt, ns, P = inf.n_tiles, sensors.shape[0], inf.tile_pix
+    u = np.empty((nt, ns, P), dtype=np.float32)
+    b = np.empty((nt, ns), dtype=np.int32)
+    s = np.empty(nt * P, dtype=np.int32)
+    _lib.check(lib.pat_table_host(*args, u.ctypes.data, b.ctypes.data, s.ctypes.data),
+               "pat_table_host")
+    info = {k: getattr(inf, k) for k, _ in _lib.PatInfo._fields_}
+    return info, u, b, s
+
+
+def wait_timeout_probe(timeout_ns=1_000_000):
+    """Run the bounded-wait probe kernel; returns the library status code."""
+    return _lib.load().pat_test_wait_timeout(int(timeout_ns))

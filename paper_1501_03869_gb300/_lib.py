@@ -1,0 +1,125 @@
+"""ctypes declarations of libpatbp.so (include/pat_bp.h).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+library.  The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1501_03869_gb300.build``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpatbp.so")
+
+PAT_OK, PAT_ERR_INVALID, PAT_ERR_OOM, PAT_ERR_CUDA = 0, 1, 2, 3
+PAT_ERR_TIMEOUT, PAT_ERR_BUSY, PAT_ERR_NOT_FOUND, PAT_PENDING = 4, 5, 6, 7
+PAT_F32, PAT_BF16, PAT_F16 = 0, 1, 2
+PAT_FLAG_COMPACT_OUT = 0x1
+PAT_FLAG_TILE_128 = 0x10
+PAT_FLAG_TILE_256 = 0x20
+
+# Every symbol include/pat_bp.h declares (checked by the CPU test suite).
+EXPORTS = (
+    "pat_status_str", "pat_last_error", "pat_bp_create", "pat_bp_reconstruct",
+    "pat_bp_preprocess", "pat_bp_gather",
+    "pat_bp_reconstruct_host", "pat_bp_reserve", "pat_bp_sync", "pat_bp_info",
+    "pat_bp_table", "pat_bp_destroy", "pat_fmm_host", "pat_table_host",
+    "pat_test_wait_timeout",
+)
+
+
+class PatGrid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double),
+                ("origin", ctypes.c_double * 3)]
+
+
+class PatInfo(ctypes.Structure):
+    _fields_ = [("n_pix", ctypes.c_int64), ("grid_total", ctypes.c_int64),
+                ("n_sensors", ctypes.c_int), ("n_samples", ctypes.c_int),
+                ("n_samples_pad", ctypes.c_int), ("tile_pix", ctypes.c_int),
+                ("n_tiles", ctypes.c_int), ("window", ctypes.c_int), ("split", ctypes.c_int),
+                ("sensor_warps", ctypes.c_int), ("table_bytes", ctypes.c_int64),
+                ("build_seconds", ctypes.c_double)]
+
+
+class PatError(RuntimeError):
+    def __init__(self, status, what, detail=""):
+        self.status = status
+        super().__init__(f"{what}: status {status} ({detail})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_u = ctypes.c_uint
+_d = ctypes.c_double
+_u64 = ctypes.c_uint64
+
+
+def load():
+    """Load libpatbp.so once; raise if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(LIB_PATH)
+        lib.pat_status_str.restype = ctypes.c_char_p
+        lib.pat_status_str.argtypes = [_i]
+        lib.pat_last_error.restype = ctypes.c_char_p
+        lib.pat_last_error.argtypes = []
+        lib.pat_bp_create.restype = _i
+        lib.pat_bp_create.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp, _vp, _d, _i, _u,
+                                      ctypes.POINTER(_vp)]
+        lib.pat_bp_reconstruct.restype = _i
+        lib.pat_bp_reconstruct.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp]
+        lib.pat_bp_preprocess.restype = _i
+        lib.pat_bp_preprocess.argtypes = [_vp, _vp, _i, _vp, _i, _vp]
+        lib.pat_bp_gather.restype = _i
+        lib.pat_bp_gather.argtypes = [_vp, _i, _vp, _vp]
+        lib.pat_bp_reconstruct_host.restype = _i
+        lib.pat_bp_reconstruct_host.argtypes = [_vp, _vp, _i, _vp, _i, _vp]
+        lib.pat_bp_reserve.restype = _i
+        lib.pat_bp_reserve.argtypes = [_vp, _i, _i]
+        lib.pat_bp_sync.restype = _i
+        lib.pat_bp_sync.argtypes = [_vp, _vp]
+        lib.pat_bp_info.restype = _i
+        lib.pat_bp_info.argtypes = [_vp, ctypes.POINTER(PatInfo)]
+        lib.pat_bp_table.restype = _i
+        lib.pat_bp_table.argtypes = [_vp, _vp, _vp, _vp]
+        lib.pat_bp_destroy.restype = _i
+        lib.pat_bp_destroy.argtypes = [_vp]
+        lib.pat_fmm_host.restype = _i
+        lib.pat_fmm_host.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _vp]
+        lib.pat_table_host.restype = _i
+        lib.pat_table_host.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp, _d, _i, _u,
+                                       ctypes.POINTER(PatInfo), _vp, _vp, _vp]
+        lib.pat_test_wait_timeout.restype = _i
+        lib.pat_test_wait_timeout.argtypes = [_u64]
+        _lib = lib
+        return lib
+
+
+def check(status, what):
+    if status != PAT_OK:
+        lib = load()
+        detail = lib.pat_last_error().decode(errors="replace")
+        raise PatError(status, what, f"{lib.pat_status_str(status).decode()}: {detail}")
+
+
+def make_grid(shape, dx, origin):
+    """pat_grid of a numpy-shaped ([nz,] ny, nx) grid."""
+    g = PatGrid()
+    g.ndim = len(shape)
+    n = list(shape[::-1]) + [1] * (3 - len(shape))
+    for d in range(3):
+        g.n[d] = int(n[d])
+        g.origin[d] = float(origin[d]) if d < len(origin) else 0.0
+    g.dx = float(dx)
+    return g

@@ -1,0 +1,396 @@
+// fmm_host.cpp -- host fast marching and travel-time table build.
+//
+// Sec. II-B: the eikonal equation |grad T|^2 = 1/c^2 is solved by fast
+// marching, one run per sensor used as the point source (ray paths are
+// reversible, so one run per sensor serves every pixel).  The update is the
+// first-order Godunov upwind discretisation sum_d max(T - a_d, 0)^2 = (h/c)^2,
+// a_d the smaller accepted neighbour along axis d.  Sec. III: this is the
+// off-line step, done once per speed map and sensor layout.
+//
+// Implementation choices of this file: a one-node ghost layer around the grid
+// (no bounds tests in the neighbour loop), an indexed binary heap with
+// decrease-key, the root of the m-axis quadratic written as
+// (S + sqrt(S^2 - m (Q - (h/c)^2))) / m, early exit once every wanted pixel is
+// accepted or the front passes the end of the record, and one std::thread per
+// core, each marching whole sensors.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <limits>
+#include <thread>
+
+#include "table.h"
+
+namespace patbp {
+
+namespace {
+constexpr uint8_t kFar = 0, kTrial = 1, kAccepted = 2, kGhost = 3;
+constexpr double kInf = std::numeric_limits<double>::infinity();
+}  // namespace
+
+FastMarcher::FastMarcher(const GridDesc& g, const std::vector<double>& slowness_h,
+                         const uint8_t* targets)
+    : g_(g) {
+  ptotal_ = 1;
+  for (int d = 0; d < 3; ++d) {
+    pn_[d] = d < g.ndim ? g.n[d] + 2 : 1;
+    pstride_[d] = ptotal_;
+    ptotal_ *= pn_[d];
+  }
+  t_.assign(ptotal_, kInf);
+  st_.assign(ptotal_, kGhost);
+  pos_.assign(ptotal_, -1);
+  hf_.assign(ptotal_, 0.0);
+  wanted_.assign(ptotal_, 0);
+  heap_.reserve(1 << 16);
+  for (int64_t v = 0; v < g.total(); ++v) {
+    int64_t pv = to_padded(v);
+    hf_[pv] = slowness_h[v];
+    wanted_[pv] = targets ? (targets[v] ? 1 : 0) : 0;
+  }
+}
+
+int64_t FastMarcher::to_padded(int64_t v) const {
+  int64_t p = 0;
+  for (int d = 0; d < 3; ++d) {
+    int64_t c = v % g_.n[d];
+    v /= g_.n[d];
+    p += (d < g_.ndim ? c + 1 : c) * pstride_[d];
+  }
+  return p;
+}
+
+bool FastMarcher::key_less(int64_t a, int64_t b) const {
+  double ta = t_[a], tb = t_[b];
+  return ta < tb || (ta == tb && a < b);
+}
+
+void FastMarcher::heap_up(int64_t i) {
+  int64_t node = heap_[i];
+  while (i > 0) {
+    int64_t up = (i - 1) >> 1;
+    if (!key_less(node, heap_[up])) break;
+    heap_[i] = heap_[up];
+    pos_[heap_[i]] = int32_t(i);
+    i = up;
+  }
+  heap_[i] = node;
+  pos_[node] = int32_t(i);
+}
+
+void FastMarcher::heap_down(int64_t i) {
+  const int64_t n = int64_t(heap_.size());
+  int64_t node = heap_[i];
+  for (;;) {
+    int64_t c = 2 * i + 1;
+    if (c >= n) break;
+    if (c + 1 < n && key_less(heap_[c + 1], heap_[c])) ++c;
+    if (!key_less(heap_[c], node)) break;
+    heap_[i] = heap_[c];
+    pos_[heap_[i]] = int32_t(i);
+    i = c;
+  }
+  heap_[i] = node;
+  pos_[node] = int32_t(i);
+}
+
+double FastMarcher::local_solve(int64_t pv, double hf) const {
+  double a[3];
+  int m = 0;
+  for (int d = 0; d < g_.ndim; ++d) {
+    const int64_t s = pstride_[d];
+    double lo = st_[pv - s] == kAccepted ? t_[pv - s] : kInf;
+    double hi = st_[pv + s] == kAccepted ? t_[pv + s] : kInf;
+    double v = lo < hi ? lo : hi;
+    if (v < kInf) a[m++] = v;
+  }
+  if (m == 0) return kInf;
+  if (m > 1 && a[1] < a[0]) std::swap(a[0], a[1]);
+  if (m > 2) {
+    if (a[2] < a[1]) std::swap(a[1], a[2]);
+    if (a[1] < a[0]) std::swap(a[0], a[1]);
+  }
+  // Grow the set of contributing axes while the root lies above the next a.
+  double S = 0.0, Q = 0.0, root = kInf;
+  const double hf2 = hf * hf;
+  for (int k = 0; k < m; ++k) {
+    S += a[k];
+    Q += a[k] * a[k];
+    const double kk = double(k + 1);
+    double disc = S * S - kk * (Q - hf2);
+    if (disc < 0.0) disc = 0.0;
+    root = (S + std::sqrt(disc)) / kk;
+    if (k + 1 == m || !(root > a[k + 1])) break;
+  }
+  return root;
+}
+
+bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_after,
+                        int64_t n_targets) {
+  // reset interior nodes; ghosts keep kGhost
+  std::fill(t_.begin(), t_.end(), kInf);
+  std::fill(pos_.begin(), pos_.end(), -1);
+  heap_.clear();
+  const int nz = g_.ndim > 2 ? g_.n[2] : 1, ny = g_.ndim > 1 ? g_.n[1] : 1, nx = g_.n[0];
+  const int oz = g_.ndim > 2 ? 1 : 0, oy = g_.ndim > 1 ? 1 : 0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j) {
+      int64_t row = (k + oz) * pstride_[2] + (j + oy) * pstride_[1] + 1;
+      std::fill(st_.begin() + row, st_.begin() + row + nx, kFar);
+    }
+
+  // Source cell: corners accepted with distance times local slowness.
+  int cell[3] = {0, 0, 0};
+  for (int d = 0; d < g_.ndim; ++d) {
+    if (g_.n[d] < 2) return false;
+    double x = (src[d] - g_.origin[d]) / g_.dx;
+    if (!(x >= 0.0) || !(x <= double(g_.n[d] - 1))) return false;
+    int i = int(std::floor(x));
+    cell[d] = std::min(i, g_.n[d] - 2);
+  }
+  int64_t wanted_left = n_targets;
+  std::vector<int64_t> seeds;
+  for (int corner = 0; corner < (1 << g_.ndim); ++corner) {
+    int64_t v = 0, mul = 1;
+    double r2 = 0.0;
+    for (int d = 0; d < g_.ndim; ++d) {
+      int i = cell[d] + ((corner >> d) & 1);
+      double off = g_.origin[d] + double(i) * g_.dx - src[d];
+      r2 += off * off;
+      v += int64_t(i) * mul;
+      mul *= g_.n[d];
+    }
+    int64_t pv = to_padded(v);
+    if (st_[pv] == kAccepted) continue;
+    t_[pv] = std::sqrt(r2) * (hf_[pv] / g_.dx);
+    st_[pv] = kAccepted;
+    seeds.push_back(pv);
+    if (wanted_[pv]) --wanted_left;
+  }
+
+  auto relax_neighbours = [&](int64_t pv) {
+    for (int d = 0; d < g_.ndim; ++d) {
+      for (int side = -1; side <= 1; side += 2) {
+        int64_t q = pv + side * pstride_[d];
+        uint8_t s = st_[q];
+        if (s == kAccepted || s == kGhost) continue;
+        double cand = local_solve(q, hf_[q]);
+        if (cand < t_[q]) {
+          t_[q] = cand;
+          if (s == kFar) {
+            st_[q] = kTrial;
+            heap_.push_back(q);
+            heap_up(int64_t(heap_.size()) - 1);
+          } else {
+            heap_up(pos_[q]);
+          }
+        }
+      }
+    }
+  };
+  for (int64_t pv : seeds) relax_neighbours(pv);
+
+  while (!heap_.empty()) {
+    if (n_targets > 0 && wanted_left <= 0) break;
+    int64_t pv = heap_[0];
+    if (t_[pv] > stop_after) break;
+    int64_t last = heap_.back();
+    heap_.pop_back();
+    pos_[pv] = -1;
+    if (!heap_.empty()) {
+      heap_[0] = last;
+      pos_[last] = 0;
+      heap_down(0);
+    }
+    st_[pv] = kAccepted;
+    if (wanted_[pv]) --wanted_left;
+    relax_neighbours(pv);
+  }
+
+  // Export accepted values; anything not accepted is +inf (never reached or
+  // beyond the early stop).
+  T.resize(size_t(g_.total()));
+  int64_t v = 0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j) {
+      int64_t row = (k + oz) * pstride_[2] + (j + oy) * pstride_[1] + 1;
+      for (int i = 0; i < nx; ++i, ++v) T[v] = st_[row + i] == kAccepted ? t_[row + i] : kInf;
+    }
+  return true;
+}
+
+// ------------------------------------------------------------ pixel order --
+namespace {
+uint64_t hilbert_key(uint32_t side, uint32_t x, uint32_t y) {
+  // Position of (x, y) along the Hilbert curve filling a side x side square
+  // (side a power of two): quadrant digits, rotating the frame per level.
+  uint64_t d = 0;
+  for (uint32_t s = side >> 1; s > 0; s >>= 1) {
+    uint32_t rx = (x & s) ? 1u : 0u;
+    uint32_t ry = (y & s) ? 1u : 0u;
+    d += uint64_t(s) * s * ((3u * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = (s - 1) - (x & (s - 1));
+        y = (s - 1) - (y & (s - 1));
+      }
+      std::swap(x, y);
+    }
+  }
+  return d;
+}
+
+uint64_t morton_key(uint32_t x, uint32_t y, uint32_t z) {
+  uint64_t k = 0;
+  for (int b = 0; b < 21; ++b) {
+    k |= uint64_t((x >> b) & 1u) << (3 * b);
+    k |= uint64_t((y >> b) & 1u) << (3 * b + 1);
+    k |= uint64_t((z >> b) & 1u) << (3 * b + 2);
+  }
+  return k;
+}
+}  // namespace
+
+std::vector<int32_t> curve_order(const GridDesc& g, const uint8_t* mask) {
+  std::vector<std::pair<uint64_t, int32_t>> keyed;
+  const int64_t total = g.total();
+  keyed.reserve(size_t(total));
+  uint32_t side = 1;
+  while (side < uint32_t(std::max(g.n[0], g.n[1]))) side <<= 1;
+  for (int64_t v = 0; v < total; ++v) {
+    if (mask && !mask[v]) continue;
+    uint32_t x = uint32_t(v % g.n[0]);
+    uint32_t y = uint32_t((v / g.n[0]) % g.n[1]);
+    uint32_t z = uint32_t(v / (int64_t(g.n[0]) * g.n[1]));
+    uint64_t key = g.ndim == 3 ? morton_key(x, y, z) : hilbert_key(side, x, y);
+    keyed.emplace_back(key, int32_t(v));
+  }
+  std::sort(keyed.begin(), keyed.end());
+  std::vector<int32_t> order(keyed.size());
+  for (size_t i = 0; i < keyed.size(); ++i) order[i] = keyed[i].second;
+  return order;
+}
+
+// ------------------------------------------------------------ table build --
+bool build_table(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
+                 const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
+                 HostTable& out, std::string& err) {
+  auto t_start = std::chrono::steady_clock::now();
+  const int64_t total = g.total();
+  std::vector<double> slowness_h(static_cast<size_t>(total));
+  for (int64_t v = 0; v < total; ++v) {
+    if (!(speed[v] > 0.0f) || !std::isfinite(speed[v])) {
+      err = "speed must be finite and > 0 at every node";
+      return false;
+    }
+    slowness_h[v] = g.dx / double(speed[v]);
+  }
+  std::vector<int32_t> order = curve_order(g, mask);
+  const int64_t n_pix = int64_t(order.size());
+  if (n_pix == 0) {
+    err = "mask selects no pixel";
+    return false;
+  }
+  const int n_tiles = int((n_pix + P - 1) / P);
+  out.P = P;
+  out.n_tiles = n_tiles;
+  out.n_sensors = n_sensors;
+  out.n_pix = n_pix;
+  out.slot_dense.assign(size_t(n_tiles) * P, -1);
+  out.slot_compact.assign(size_t(n_tiles) * P, -1);
+  std::vector<int32_t> rank(size_t(total), -1);
+  {
+    int32_t r = 0;
+    for (int64_t v = 0; v < total; ++v)
+      if (!mask || mask[v]) rank[v] = r++;
+  }
+  for (int64_t i = 0; i < n_pix; ++i) {
+    out.slot_dense[i] = order[i];
+    out.slot_compact[i] = rank[order[i]];
+  }
+  out.zero_runs.clear();
+  if (!compact_out && mask) {
+    int64_t v = 0;
+    while (v < total) {
+      if (mask[v]) { ++v; continue; }
+      int64_t s = v;
+      while (v < total && !mask[v]) ++v;
+      out.zero_runs.push_back(int32_t(s));
+      out.zero_runs.push_back(int32_t(v - s));
+    }
+  }
+  out.u.assign(size_t(n_tiles) * n_sensors * P, kOutOfRecord);
+  out.base.assign(size_t(n_tiles) * n_sensors, 0);
+  out.len.assign(size_t(n_tiles) * n_sensors, 0);
+
+  std::vector<uint8_t> wanted(size_t(total), 0);
+  for (int32_t v : order) wanted[v] = 1;
+  const double last_u = double(n_samples - 1);
+  const double stop_after = last_u * dt * (1.0 + 1e-9);
+
+  unsigned n_threads = std::max(1u, std::thread::hardware_concurrency());
+  n_threads = std::min<unsigned>(n_threads, unsigned(n_sensors));
+  std::atomic<int> next{0};
+  std::atomic<bool> failed{false};
+  std::vector<int> span_max(n_threads, 0);
+  auto worker = [&](unsigned tid) {
+    FastMarcher fm(g, slowness_h, wanted.data());
+    std::vector<double> T;
+    int span_local = 0;
+    for (;;) {
+      int s = next.fetch_add(1);
+      if (s >= n_sensors || failed.load()) break;
+      if (!fm.solve(sensors + 3 * s, T, stop_after, n_pix)) {
+        failed.store(true);
+        break;
+      }
+      for (int t = 0; t < n_tiles; ++t) {
+        const int32_t* slot = out.slot_dense.data() + size_t(t) * P;
+        int64_t lo = std::numeric_limits<int64_t>::max(), hi = -1;
+        for (int p = 0; p < P; ++p) {
+          if (slot[p] < 0) continue;
+          double u = T[slot[p]] / dt;
+          if (!(u <= last_u)) continue;  // after the record (or unreached)
+          int64_t i = int64_t(std::floor(u));
+          lo = std::min(lo, i);
+          hi = std::max(hi, i);
+        }
+        float* urow = out.u.data() + (size_t(t) * n_sensors + s) * P;
+        if (hi < 0) {
+          out.base[size_t(t) * n_sensors + s] = 0;
+          continue;
+        }
+        int64_t base = lo & ~int64_t(7);
+        // window [base, base + len) holds floor(u), floor(u) + 1 and one more
+        // sample for an offset that rounds up to the next integer in FP32
+        int len = (int(hi - base + 3) + 7) & ~7;
+        out.base[size_t(t) * n_sensors + s] = int32_t(base);
+        out.len[size_t(t) * n_sensors + s] = uint16_t(len);
+        span_local = std::max(span_local, len);
+        for (int p = 0; p < P; ++p) {
+          if (slot[p] < 0) continue;
+          double u = T[slot[p]] / dt;
+          if (!(u <= last_u)) continue;
+          urow[p] = float(u - double(base));
+        }
+      }
+    }
+    span_max[tid] = span_local;
+  };
+  std::vector<std::thread> pool;
+  for (unsigned i = 0; i < n_threads; ++i) pool.emplace_back(worker, i);
+  for (auto& th : pool) th.join();
+  if (failed.load()) {
+    err = "a sensor lies outside the grid box";
+    return false;
+  }
+  int span = 8;
+  for (int s : span_max) span = std::max(span, s);
+  out.W = span;
+  out.build_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  return true;
+}
+
+}  // namespace patbp

@@ -1,0 +1,581 @@
+// pat_bp.cu -- C ABI of the back-projection library (include/pat_bp.h).
+//
+// Off-line step (Sec. III): pat_bp_create runs the host fast marching of
+// Sec. II-B for every sensor, lays the travel times out for the gather kernel
+// and uploads them once.  On-line step: pat_bp_reconstruct enqueues the
+// preprocessing kernel (Eq. (BP) integrand) and the gather kernel on the
+// caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pat_bp.h"
+#include "kernels.cuh"
+#include "table.h"
+
+using namespace patbp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pat_status fail(pat_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+pat_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return PAT_ERR_CUDA;
+}
+
+#define PAT_CUDA(call)                                     \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct pat_bp_s {
+  int device = 0;
+  int n_sm = 0;
+  GridDesc g;
+  int ns = 0, ns_pad = 0, nt = 0, nt_pad = 0;
+  double dt = 0.0;
+  unsigned flags = 0;
+  bool compact = false;
+  int P = 128, SW = 4, n_tiles = 0, W = 0, split = 1, split_len = 0;
+  int64_t n_pix = 0, grid_total = 0, out_stride = 0;
+  int n_zero_runs = 0;
+  double build_seconds = 0.0;
+  std::vector<uint16_t> win_len;      // host copy of the window lengths [tile][sensor]
+  int pre_frames = 0;                 // frames held by the integrand buffer
+  int pre_fmt = 0;                    // their storage format
+  int wst_cache[33] = {0};            // stage window bound per sensors-per-stage
+  float* d_u = nullptr;
+  int32_t* d_base = nullptr;
+  int32_t* d_slot = nullptr;
+  int32_t* d_zero_runs = nullptr;
+  float* d_w = nullptr;
+  int* d_status = nullptr;
+  void* d_b = nullptr;
+  size_t b_cap = 0;
+  float* d_m = nullptr;
+  size_t m_cap = 0;
+  // staging of pat_bp_reconstruct_host
+  cudaStream_t own_stream = nullptr;
+  void* d_sig = nullptr;
+  size_t sig_cap = 0;
+  float* d_scales = nullptr;
+  size_t scales_cap = 0;
+  float* d_out = nullptr;
+  size_t out_cap = 0;
+  std::mutex mu;
+};
+
+extern "C" const char* pat_status_str(pat_status s) {
+  switch (s) {
+    case PAT_OK: return "ok";
+    case PAT_ERR_INVALID: return "invalid argument";
+    case PAT_ERR_OOM: return "out of memory";
+    case PAT_ERR_CUDA: return "CUDA error";
+    case PAT_ERR_TIMEOUT: return "timeout";
+    case PAT_ERR_BUSY: return "busy";
+    case PAT_ERR_NOT_FOUND: return "not found";
+    case PAT_PENDING: return "pending";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* pat_last_error(void) { return g_last_error.c_str(); }
+
+static bool grid_from_abi(const pat_grid* pg, GridDesc& g, std::string& err) {
+  if (!pg || (pg->ndim != 2 && pg->ndim != 3)) {
+    err = "grid.ndim must be 2 or 3";
+    return false;
+  }
+  g.ndim = pg->ndim;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = d < pg->ndim ? pg->n[d] : 1;
+    g.origin[d] = pg->origin[d];
+    if (g.n[d] < 1 || (d < pg->ndim && g.n[d] < 2)) {
+      err = "grid needs at least 2 nodes along every active axis";
+      return false;
+    }
+  }
+  g.dx = pg->dx;
+  if (!(g.dx > 0.0) || !std::isfinite(g.dx)) {
+    err = "grid.dx must be > 0";
+    return false;
+  }
+  if (g.total() > (int64_t(1) << 31) - 1) {
+    err = "grid too large (2^31 nodes at most)";
+    return false;
+  }
+  return true;
+}
+
+static void free_handle(pat_bp_t h) {
+  if (!h) return;
+  cudaFree(h->d_u);
+  cudaFree(h->d_base);
+  cudaFree(h->d_slot);
+  cudaFree(h->d_zero_runs);
+  cudaFree(h->d_w);
+  cudaFree(h->d_status);
+  cudaFree(h->d_b);
+  cudaFree(h->d_m);
+  cudaFree(h->d_sig);
+  cudaFree(h->d_scales);
+  cudaFree(h->d_out);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+}
+
+template <typename T>
+static pat_status upload(T** dst, const std::vector<T>& src, const char* what) {
+  size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+  if (e != cudaSuccess) return fail(PAT_ERR_OOM, std::string("cudaMalloc ") + what);
+  if (!src.empty()) PAT_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* grid,
+                                    const double* sensors_host, int n_sensors,
+                                    const uint8_t* mask_host, const float* weights_host,
+                                    double dt, int n_samples, unsigned flags, pat_bp_t* out) {
+  if (!out) return fail(PAT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!speed_host || !sensors_host) return fail(PAT_ERR_INVALID, "speed/sensors NULL");
+  if (n_sensors < 1 || n_sensors > (1 << 20)) return fail(PAT_ERR_INVALID, "n_sensors out of range");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(PAT_ERR_INVALID, "dt must be > 0");
+  if (n_samples < 2 || n_samples > 32768) return fail(PAT_ERR_INVALID, "n_samples must be 2..32768");
+  GridDesc g;
+  std::string err;
+  if (!grid_from_abi(grid, g, err)) return fail(PAT_ERR_INVALID, err);
+  for (int s = 0; s < n_sensors; ++s)
+    for (int d = 0; d < g.ndim; ++d) {
+      double x = (sensors_host[3 * s + d] - g.origin[d]) / g.dx;
+      if (!(x >= 0.0 && x <= double(g.n[d] - 1)))
+        return fail(PAT_ERR_INVALID, "sensor " + std::to_string(s) + " lies outside the grid");
+    }
+
+  pat_bp_t h = new (std::nothrow) pat_bp_s();
+  if (!h) return fail(PAT_ERR_OOM, "handle");
+  PAT_CUDA(cudaGetDevice(&h->device));
+  cudaDeviceProp prop;
+  PAT_CUDA(cudaGetDeviceProperties(&prop, h->device));
+  h->n_sm = prop.multiProcessorCount;
+  h->g = g;
+  h->ns = n_sensors;
+  h->ns_pad = round_up(n_sensors, 4);
+  h->nt = n_samples;
+  h->nt_pad = round_up(n_samples + 1, 8);
+  h->dt = dt;
+  h->flags = flags;
+  h->compact = (flags & PAT_FLAG_COMPACT_OUT) != 0;
+  h->P = (flags & PAT_FLAG_TILE_256) ? 256 : 128;
+  h->SW = h->P == 128 ? 4 : 2;
+  h->grid_total = g.total();
+
+  HostTable tab;
+  if (!build_table(speed_host, g, sensors_host, n_sensors, mask_host, dt, n_samples, h->P,
+                   h->compact, tab, err)) {
+    free_handle(h);
+    return fail(PAT_ERR_INVALID, err);
+  }
+  h->n_tiles = tab.n_tiles;
+  h->n_pix = tab.n_pix;
+  h->W = tab.W;
+  h->build_seconds = tab.build_seconds;
+  h->out_stride = h->compact ? h->n_pix : h->grid_total;
+  h->n_zero_runs = int(tab.zero_runs.size() / 2);
+  h->win_len = tab.len;
+
+  // Sensor splits (cluster ranks) per tile: enough CTAs for two per SM.  The
+  // split is fixed per handle so the summation order never changes.
+  int split = 1;
+  while (split < 8 && int64_t(h->n_tiles) * split < 2 * int64_t(h->n_sm) &&
+         (n_sensors + 2 * split - 1) / (2 * split) >= 4)
+    split *= 2;
+  h->split = split;
+  h->split_len = round_up((n_sensors + split - 1) / split, 4);
+
+  std::vector<float> w(n_sensors);
+  for (int s = 0; s < n_sensors; ++s) w[s] = weights_host ? weights_host[s] : 1.0f / float(n_sensors);
+
+  // device form of base and window length: base in the low 16 bits, length
+  // in the high 16 bits (n_samples <= 32768 keeps both in range)
+  std::vector<int32_t> packed(tab.base.size());
+  for (size_t i = 0; i < packed.size(); ++i)
+    packed[i] = int32_t(uint32_t(tab.base[i]) | (uint32_t(tab.len[i]) << 16));
+  pat_status st;
+  if ((st = upload(&h->d_u, tab.u, "table")) != PAT_OK ||
+      (st = upload(&h->d_base, packed, "bases")) != PAT_OK ||
+      (st = upload(&h->d_slot, h->compact ? tab.slot_compact : tab.slot_dense, "slots")) != PAT_OK ||
+      (st = upload(&h->d_zero_runs, tab.zero_runs, "zero runs")) != PAT_OK ||
+      (st = upload(&h->d_w, w, "weights")) != PAT_OK) {
+    free_handle(h);
+    return st;
+  }
+  if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess) {
+    free_handle(h);
+    return fail(PAT_ERR_OOM, "status word");
+  }
+  cudaMemset(h->d_status, 0, sizeof(int));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_handle(h);
+    return cuda_fail(e, "create");
+  }
+  *out = h;
+  return PAT_OK;
+}
+
+static int fmt_for(pat_dtype dt) {
+  return dt == PAT_F32 ? kBF32 : (dt == PAT_BF16 ? kBBF16P : kBF16P);
+}
+
+static pat_status ensure_buffers(pat_bp_t h, int n_frames) {
+  const size_t b_need = (size_t(n_frames) * h->ns * h->nt_pad + size_t(h->W) + 64) * 4;
+  if (b_need > h->b_cap) {
+    cudaFree(h->d_b);
+    h->d_b = nullptr;
+    h->b_cap = 0;
+    if (cudaMalloc(&h->d_b, b_need) != cudaSuccess) return fail(PAT_ERR_OOM, "integrand buffer");
+    PAT_CUDA(cudaMemset(h->d_b, 0, b_need));
+    h->b_cap = b_need;
+  }
+  const size_t m_need = size_t(n_frames) * h->ns_pad * sizeof(float);
+  if (m_need > h->m_cap) {
+    cudaFree(h->d_m);
+    h->d_m = nullptr;
+    h->m_cap = 0;
+    if (cudaMalloc(&h->d_m, m_need) != cudaSuccess) return fail(PAT_ERR_OOM, "multipliers");
+    PAT_CUDA(cudaMemset(h->d_m, 0, m_need));
+    h->m_cap = m_need;
+  }
+  return PAT_OK;
+}
+
+// Largest sum of window lengths over the S-sensor stages of any tile: the
+// window entries one pipeline stage must hold per frame.
+static int stage_window(pat_bp_t h, int S) {
+  if (S >= 1 && S <= 32 && h->wst_cache[S]) return h->wst_cache[S];
+  int best = 8;
+  for (int t = 0; t < h->n_tiles; ++t) {
+    const uint16_t* len = h->win_len.data() + size_t(t) * h->ns;
+    for (int r = 0; r < h->split; ++r) {
+      const int sb = r * h->split_len, se = std::min(h->ns, sb + h->split_len);
+      for (int s0 = sb; s0 < se; s0 += S) {
+        int sum = 0;
+        for (int s = s0; s < std::min(se, s0 + S); ++s) sum += len[s];
+        best = std::max(best, sum);
+      }
+    }
+  }
+  best = round_up(best, 8);
+  if (S >= 1 && S <= 32) h->wst_cache[S] = best;
+  return best;
+}
+
+// Launch shape for a frame count: frames per CTA, sensors per stage, stages.
+static GatherConfig pick_config(pat_bp_t h, int n_frames, int* wst) {
+  GatherConfig c;
+  c.P = h->P;
+  c.SW = h->SW;
+  c.FB = n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1));
+  c.S = c.FB == 1 ? 16 : 8;
+  const size_t budget = 110 * 1024;
+  c.stages = 6;
+  for (;;) {
+    *wst = stage_window(h, c.S);
+    while (c.stages > 2 && gather_smem_bytes(c, 0, *wst) > budget) --c.stages;
+    if (gather_smem_bytes(c, 0, *wst) <= budget || c.S <= c.SW) break;
+    c.S -= c.SW;
+  }
+  return c;
+}
+
+extern "C" pat_status pat_bp_reserve(pat_bp_t h, int max_frames, pat_dtype dtype) {
+  if (!h || max_frames < 1) return fail(PAT_ERR_INVALID, "bad handle or frame count");
+  (void)dtype;
+  std::lock_guard<std::mutex> lk(h->mu);
+  PAT_CUDA(cudaSetDevice(h->device));
+  return ensure_buffers(h, max_frames);
+}
+
+static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                                    const float* scales_dev, int n_frames, cudaStream_t stream) {
+  if (!signals_dev) return fail(PAT_ERR_INVALID, "signals NULL");
+  if (n_frames < 1 || n_frames > 65535) return fail(PAT_ERR_INVALID, "n_frames must be 1..65535");
+  if (dtype != PAT_F32 && dtype != PAT_BF16 && dtype != PAT_F16)
+    return fail(PAT_ERR_INVALID, "unknown dtype");
+  if (dtype != PAT_F32 && !scales_dev) return fail(PAT_ERR_INVALID, "16-bit signals need scales");
+  pat_status st = ensure_buffers(h, n_frames);
+  if (st != PAT_OK) return st;
+  PreParams pp;
+  pp.sig = signals_dev;
+  pp.scales = scales_dev;
+  pp.weights = h->d_w;
+  pp.b = h->d_b;
+  pp.m = h->d_m;
+  pp.dtype = int(dtype);
+  pp.fmt = fmt_for(dtype);
+  pp.n_sensors = h->ns;
+  pp.n_sensors_pad = h->ns_pad;
+  pp.n_t = h->nt;
+  pp.n_t_pad = h->nt_pad;
+  pp.n_frames = n_frames;
+  cudaError_t e = launch_preprocess(pp, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
+  h->pre_frames = n_frames;
+  h->pre_fmt = pp.fmt;
+  return PAT_OK;
+}
+
+static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaStream_t stream) {
+  if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
+  if (n_frames < 1 || n_frames > h->pre_frames)
+    return fail(PAT_ERR_INVALID, "gather needs a preprocess of at least n_frames frames first");
+  int wst = 0;
+  GatherConfig c = pick_config(h, n_frames, &wst);
+  GatherParams gp;
+  gp.u = h->d_u;
+  gp.base = h->d_base;
+  gp.slot = h->d_slot;
+  gp.zero_runs = h->d_zero_runs;
+  gp.n_zero_runs = h->n_zero_runs;
+  gp.b = h->d_b;
+  gp.m = h->d_m;
+  gp.out = out_dev;
+  gp.out_stride = h->out_stride;
+  gp.n_sensors = h->ns;
+  gp.n_sensors_pad = h->ns_pad;
+  gp.n_t_pad = h->nt_pad;
+  gp.Wst = wst;
+  gp.n_tiles = h->n_tiles;
+  gp.n_frames = n_frames;
+  gp.S = c.S;
+  gp.stages = c.stages;
+  gp.split = h->split;
+  gp.split_len = h->split_len;
+  gp.status = h->d_status;
+  gp.timeout_ns = 2000000000ull;
+  cudaError_t e = launch_gather(c, h->pre_fmt, gp, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+  return PAT_OK;
+}
+
+static pat_status reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                                     const float* scales_dev, int n_frames, float* out_dev,
+                                     cudaStream_t stream) {
+  if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
+  pat_status st = preprocess_locked(h, signals_dev, dtype, scales_dev, n_frames, stream);
+  if (st != PAT_OK) return st;
+  return gather_locked(h, n_frames, out_dev, stream);
+}
+
+extern "C" pat_status pat_bp_preprocess(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                                        const float* scales_dev, int n_frames,
+                                        pat_stream_t stream) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  PAT_CUDA(cudaSetDevice(h->device));
+  return preprocess_locked(h, signals_dev, dtype, scales_dev, n_frames,
+                           static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pat_status pat_bp_gather(pat_bp_t h, int n_frames, float* out_dev, pat_stream_t stream) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  PAT_CUDA(cudaSetDevice(h->device));
+  return gather_locked(h, n_frames, out_dev, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pat_status pat_bp_reconstruct(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                                         const float* scales_dev, int n_frames, float* out_dev,
+                                         pat_stream_t stream) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  PAT_CUDA(cudaSetDevice(h->device));
+  return reconstruct_locked(h, signals_dev, dtype, scales_dev, n_frames, out_dev,
+                            static_cast<cudaStream_t>(stream));
+}
+
+static pat_status grow(void** p, size_t* cap, size_t need, const char* what) {
+  if (need <= *cap) return PAT_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) return fail(PAT_ERR_OOM, what);
+  *cap = need;
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_bp_reconstruct_host(pat_bp_t h, const void* signals_host, pat_dtype dtype,
+                                              const float* scales_host, int n_frames,
+                                              float* out_host) {
+  if (!h || !signals_host || !out_host) return fail(PAT_ERR_INVALID, "NULL argument");
+  if (n_frames < 1) return fail(PAT_ERR_INVALID, "n_frames < 1");
+  std::lock_guard<std::mutex> lk(h->mu);
+  PAT_CUDA(cudaSetDevice(h->device));
+  if (!h->own_stream) PAT_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+  const size_t esz = dtype == PAT_F32 ? 4 : 2;
+  const size_t sig_bytes = size_t(n_frames) * h->ns * h->nt * esz;
+  const size_t sc_bytes = size_t(n_frames) * h->ns * sizeof(float);
+  const size_t out_bytes = size_t(n_frames) * h->out_stride * sizeof(float);
+  pat_status st;
+  if ((st = grow(&h->d_sig, &h->sig_cap, sig_bytes, "signal staging")) != PAT_OK) return st;
+  if (scales_host &&
+      (st = grow(reinterpret_cast<void**>(&h->d_scales), &h->scales_cap, sc_bytes, "scales")) != PAT_OK)
+    return st;
+  if ((st = grow(reinterpret_cast<void**>(&h->d_out), &h->out_cap, out_bytes, "output staging")) != PAT_OK)
+    return st;
+  cudaStream_t s = h->own_stream;
+  PAT_CUDA(cudaMemcpyAsync(h->d_sig, signals_host, sig_bytes, cudaMemcpyHostToDevice, s));
+  if (scales_host) PAT_CUDA(cudaMemcpyAsync(h->d_scales, scales_host, sc_bytes, cudaMemcpyHostToDevice, s));
+  st = reconstruct_locked(h, h->d_sig, dtype, scales_host ? h->d_scales : nullptr, n_frames, h->d_out, s);
+  if (st != PAT_OK) return st;
+  PAT_CUDA(cudaMemcpyAsync(out_host, h->d_out, out_bytes, cudaMemcpyDeviceToHost, s));
+  PAT_CUDA(cudaStreamSynchronize(s));
+  int flag = 0;
+  PAT_CUDA(cudaMemcpy(&flag, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    cudaMemset(h->d_status, 0, sizeof(int));
+    return fail(PAT_ERR_TIMEOUT, "a device wait ran out of time");
+  }
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_bp_sync(pat_bp_t h, pat_stream_t stream) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  PAT_CUDA(cudaSetDevice(h->device));
+  PAT_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int flag = 0;
+  PAT_CUDA(cudaMemcpy(&flag, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    PAT_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
+    return fail(PAT_ERR_TIMEOUT, "a device wait ran out of time");
+  }
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_bp_info(pat_bp_t h, pat_bp_info_t* info) {
+  if (!h || !info) return fail(PAT_ERR_INVALID, "NULL argument");
+  info->n_pix = h->n_pix;
+  info->grid_total = h->grid_total;
+  info->n_sensors = h->ns;
+  info->n_samples = h->nt;
+  info->n_samples_pad = h->nt_pad;
+  info->tile_pix = h->P;
+  info->n_tiles = h->n_tiles;
+  info->window = h->W;
+  info->split = h->split;
+  info->sensor_warps = h->SW;
+  info->table_bytes = int64_t(h->n_tiles) * h->ns * h->P * 4;
+  info->build_seconds = h->build_seconds;
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_bp_table(pat_bp_t h, float* u_host, int32_t* base_host, int32_t* pix_host) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  PAT_CUDA(cudaSetDevice(h->device));
+  const size_t n = size_t(h->n_tiles) * h->ns;
+  if (u_host) PAT_CUDA(cudaMemcpy(u_host, h->d_u, n * h->P * 4, cudaMemcpyDeviceToHost));
+  if (base_host) {
+    PAT_CUDA(cudaMemcpy(base_host, h->d_base, n * 4, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) base_host[i] &= 0xffff;
+  }
+  if (pix_host) PAT_CUDA(cudaMemcpy(pix_host, h->d_slot, size_t(h->n_tiles) * h->P * 4, cudaMemcpyDeviceToHost));
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_bp_destroy(pat_bp_t h) {
+  if (!h) return PAT_OK;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  free_handle(h);
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_fmm_host(const float* speed_host, const pat_grid* grid, const double* src_xyz,
+                                   double* T_out) {
+  if (!speed_host || !src_xyz || !T_out) return fail(PAT_ERR_INVALID, "NULL argument");
+  GridDesc g;
+  std::string err;
+  if (!grid_from_abi(grid, g, err)) return fail(PAT_ERR_INVALID, err);
+  std::vector<double> slow(static_cast<size_t>(g.total()));
+  for (int64_t v = 0; v < g.total(); ++v) {
+    if (!(speed_host[v] > 0.0f)) return fail(PAT_ERR_INVALID, "speed must be > 0");
+    slow[v] = g.dx / double(speed_host[v]);
+  }
+  FastMarcher fm(g, slow, nullptr);
+  std::vector<double> T;
+  if (!fm.solve(src_xyz, T, std::numeric_limits<double>::infinity(), 0))
+    return fail(PAT_ERR_INVALID, "source outside the grid");
+  std::memcpy(T_out, T.data(), T.size() * sizeof(double));
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_table_host(const float* speed_host, const pat_grid* grid,
+                                     const double* sensors_host, int n_sensors,
+                                     const uint8_t* mask_host, double dt, int n_samples,
+                                     unsigned flags, pat_bp_info_t* info, float* u_host,
+                                     int32_t* base_host, int32_t* slot_host) {
+  if (!speed_host || !sensors_host || !info) return fail(PAT_ERR_INVALID, "NULL argument");
+  if (n_sensors < 1 || !(dt > 0.0) || n_samples < 2 || n_samples > 32768)
+    return fail(PAT_ERR_INVALID, "bad sizes");
+  GridDesc g;
+  std::string err;
+  if (!grid_from_abi(grid, g, err)) return fail(PAT_ERR_INVALID, err);
+  const bool compact = (flags & PAT_FLAG_COMPACT_OUT) != 0;
+  const int P = (flags & PAT_FLAG_TILE_256) ? 256 : 128;
+  HostTable tab;
+  if (!build_table(speed_host, g, sensors_host, n_sensors, mask_host, dt, n_samples, P, compact, tab,
+                   err))
+    return fail(PAT_ERR_INVALID, err);
+  std::memset(info, 0, sizeof(*info));
+  info->n_pix = tab.n_pix;
+  info->grid_total = g.total();
+  info->n_sensors = n_sensors;
+  info->n_samples = n_samples;
+  info->n_samples_pad = round_up(n_samples + 1, 8);
+  info->tile_pix = P;
+  info->n_tiles = tab.n_tiles;
+  info->window = tab.W;
+  info->table_bytes = int64_t(tab.u.size()) * 4;
+  info->build_seconds = tab.build_seconds;
+  if (u_host) std::memcpy(u_host, tab.u.data(), tab.u.size() * 4);
+  if (base_host) std::memcpy(base_host, tab.base.data(), tab.base.size() * 4);
+  if (slot_host) {
+    const std::vector<int32_t>& sl = compact ? tab.slot_compact : tab.slot_dense;
+    std::memcpy(slot_host, sl.data(), sl.size() * 4);
+  }
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_test_wait_timeout(uint64_t timeout_ns) {
+  int* d = nullptr;
+  PAT_CUDA(cudaMalloc(&d, sizeof(int)));
+  cudaMemset(d, 0, sizeof(int));
+  cudaError_t e = launch_wait_probe(d, timeout_ns, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  return flag ? PAT_ERR_TIMEOUT : PAT_OK;
+}

@@ -1,0 +1,93 @@
+// table.h -- host-side travel-time table of the back projection (internal).
+//
+// The table is the product of the off-line step of Sec. III: fast-marching
+// arrival times T_s(r) (Sec. II-B) for every sensor s and every reconstructed
+// pixel r, stored for the on-line gather of Eq. (BP).
+//
+// Layout (all row-major, built for the gather kernel's TMA staging):
+//   pixels are ordered along a space-filling curve (Hilbert in 2-D, Morton in
+//   3-D) and cut into tiles of P consecutive pixels, so the pixels of a tile
+//   are close in space and their arrival times from one sensor span few
+//   samples;
+//   u[tile][sensor][P]   FP32 offset u = T/dt - base, or kOutOfRecord when the
+//                        arrival falls after the last sample (or the slot is
+//                        padding);
+//   base[tile][sensor]   int32 first sample of the window the tile needs from
+//                        that sensor, a multiple of 8;
+//   len[tile][sensor]    samples of that window, a multiple of 8 (0 when no
+//                        pixel of the tile hears the sensor within the
+//                        record); every in-record offset has floor(u) + 2 < len;
+//   W                    the largest len (at least 8).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace patbp {
+
+constexpr float kOutOfRecord = 1.0e30f;
+
+struct GridDesc {
+  int ndim = 2;
+  int n[3] = {1, 1, 1};
+  double dx = 0.0;
+  double origin[3] = {0.0, 0.0, 0.0};
+  int64_t total() const { return int64_t(n[0]) * n[1] * n[2]; }
+};
+
+struct HostTable {
+  int P = 0;
+  int n_tiles = 0;
+  int n_sensors = 0;
+  int W = 0;
+  int64_t n_pix = 0;
+  std::vector<float> u;             // [n_tiles][n_sensors][P]
+  std::vector<int32_t> base;        // [n_tiles][n_sensors]
+  std::vector<uint16_t> len;        // [n_tiles][n_sensors]
+  std::vector<int32_t> slot_dense;  // [n_tiles * P] dense grid index or -1
+  std::vector<int32_t> slot_compact;// [n_tiles * P] raster rank among mask pixels or -1
+  std::vector<int32_t> zero_runs;   // pairs (start, length) of non-mask runs of the grid
+  double build_seconds = 0.0;
+};
+
+// First-order Godunov fast marching from one point source (Sec. II-B) on the
+// host in FP64.  slowness_h[v] = dx / c(v); `targets` (optional, total()
+// bytes, nonzero = wanted) marks the nodes the caller needs.  solve() writes
+// total() values to T; nodes never accepted hold +inf.  The march ends early
+// once the smallest tentative time exceeds `stop_after` (s) or once all
+// n_targets wanted nodes are accepted (n_targets = 0: never); values of
+// accepted nodes never depend on either early stop.
+class FastMarcher {
+ public:
+  FastMarcher(const GridDesc& g, const std::vector<double>& slowness_h, const uint8_t* targets);
+  bool solve(const double* src, std::vector<double>& T, double stop_after, int64_t n_targets);
+
+ private:
+  GridDesc g_;
+  int pn_[3];            // padded extents (one ghost layer per active side)
+  int64_t pstride_[3];
+  int64_t ptotal_;
+  std::vector<double> t_;     // padded arrival times
+  std::vector<uint8_t> st_;   // padded states
+  std::vector<int32_t> pos_;  // heap position of each padded node, -1 if absent
+  std::vector<int64_t> heap_; // padded node ids
+  std::vector<double> hf_;    // padded dx / c
+  std::vector<uint8_t> wanted_;
+  int64_t to_padded(int64_t v) const;
+  void heap_up(int64_t i);
+  void heap_down(int64_t i);
+  bool key_less(int64_t a, int64_t b) const;
+  double local_solve(int64_t pv, double hf) const;
+};
+
+// Builds the table for every sensor with all host threads.
+bool build_table(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
+                 const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
+                 HostTable& out, std::string& err);
+
+// Pixel order used by the table: mask pixels (dense indices) sorted along the
+// space-filling curve of the grid.
+std::vector<int32_t> curve_order(const GridDesc& g, const uint8_t* mask);
+
+}  // namespace patbp
