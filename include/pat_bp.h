@@ -70,7 +70,7 @@ typedef struct {
   int tile_pix;         /* P: pixels per tile                                 */
   int n_tiles;
   int window;           /* W: samples of one sensor a tile can touch          */
-  int split;            /* sensor splits per tile (thread-block cluster size) */
+  int split;            /* sensor segments per tile (64 sensors each)         */
   int sensor_warps;     /* warps that share a tile's sensors inside one CTA   */
   int64_t table_bytes;  /* device bytes of the travel-time table              */
   double build_seconds; /* host time of the fast-marching table build         */

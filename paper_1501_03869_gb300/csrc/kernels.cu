@@ -6,32 +6,31 @@
 //                      pairs with a per-row scale.  Since t_k / dt = k the
 //                      interior value is 2 p_k - k (p_{k+1} - p_{k-1}).
 //   gather_kernel      out[f][r] = sum_s w_s * b_{f,s}(T_s(r)/dt) with linear
-//                      interpolation (Sec. II-C).  One CTA owns a tile of P
-//                      pixels, a contiguous range of sensors (one rank of a
-//                      thread-block cluster) and FB frames.  A producer warp
-//                      streams, per stage of S sensors, the tile's table block
-//                      u[S][P], the multipliers and each sensor's window of
-//                      integrand samples (packed back to back) into shared
-//                      memory with 1-D bulk copies (cp.async.bulk) completing
-//                      on mbarriers; consumer
-//                      warps interpolate from shared memory and accumulate in
-//                      FP32 registers.  Sensor phases inside the CTA are summed
-//                      in fixed order through shared memory, cluster ranks in
-//                      fixed order through distributed shared memory, so the
-//                      result does not depend on timing or on batch size.
+//                      interpolation (Sec. II-C).  Persistent: the work of one
+//                      launch is a sequence of units (instance, frame group,
+//                      tile of P pixels, segment of G sensors), cut into one
+//                      contiguous range per CTA.  A producer warp streams, per
+//                      stage of S sensors, the tile's table rows u[S][P], the
+//                      multipliers and every sensor's window of integrand rows
+//                      (packed back to back, FB frames per row) into shared
+//                      memory with 1-D bulk copies (cp.async.bulk) completing on
+//                      mbarriers; the windows' bases are fetched one unit ahead.
+//                      Consumer warps interpolate from shared memory and
+//                      accumulate in FP32 registers.  Sensor phases are summed
+//                      in fixed order through shared memory and segments in
+//                      fixed order by the last CTA to finish a tile, so the
+//                      result depends neither on timing nor on how frames or
+//                      instances are batched.
 //
 // Every wait on an mbarrier is bounded by a wall-clock limit; on expiry the CTA
 // records kStatusTimeout, drains its own copies in flight (bounded again) and
 // exits without touching the output's remaining values.
-#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cstdio>
 
 #include "kernels.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace patbp {
 
@@ -104,6 +103,29 @@ __device__ __forceinline__ void named_barrier(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
+__device__ __forceinline__ void named_barrier_arrive(int id, int threads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Hand-off barriers of the double-buffered unit sums, with literal ids so the
+// compiler reserves only the ids it sees: "full" 1/2 and "free" 3/4 per buffer.
+__device__ __forceinline__ void red_full_sync(int buf, int n) {
+  if (buf) asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
+  else asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void red_full_arrive(int buf, int n) {
+  if (buf) asm volatile("bar.arrive 2, %0;" ::"r"(n) : "memory");
+  else asm volatile("bar.arrive 1, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void red_free_sync(int buf, int n) {
+  if (buf) asm volatile("bar.sync 4, %0;" ::"r"(n) : "memory");
+  else asm volatile("bar.sync 3, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void red_free_arrive(int buf, int n) {
+  if (buf) asm volatile("bar.arrive 4, %0;" ::"r"(n) : "memory");
+  else asm volatile("bar.arrive 3, %0;" ::"r"(n) : "memory");
+}
+
 // ---------------------------------------------------------- preprocessing --
 template <int DT>
 __device__ __forceinline__ float load_sample(const void* sig, int64_t i) {
@@ -116,312 +138,486 @@ __device__ __forceinline__ float load_sample(const void* sig, int64_t i) {
   }
 }
 
-// b_k from the pressure row in shared memory (zero past the record).
-__device__ __forceinline__ float integrand(const float* prow, int k, int n) {
+// b_k of one pressure row (zero past the record): 2 p_k - 2 t_k dp/dt with
+// t_k / dt = k, central difference inside, one-sided at both ends.
+template <int DT>
+__device__ __forceinline__ float integrand(const void* sig, int64_t row0, float sc, int k, int n) {
   if (k >= n) return 0.0f;
-  const float pk = prow[k];
+  const float pk = load_sample<DT>(sig, row0 + k) * sc;
   if (k == 0) return 2.0f * pk;
-  if (k == n - 1) return fmaf(-2.0f * float(k), pk - prow[k - 1], 2.0f * pk);
-  return fmaf(-float(k), prow[k + 1] - prow[k - 1], 2.0f * pk);
+  const float pm = load_sample<DT>(sig, row0 + k - 1) * sc;
+  if (k == n - 1) return fmaf(-2.0f * float(k), pk - pm, 2.0f * pk);
+  const float pp = load_sample<DT>(sig, row0 + k + 1) * sc;
+  return fmaf(-float(k), pp - pm, 2.0f * pk);
 }
 
-__device__ __forceinline__ float block_max(float v, float* scratch) {
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) scratch[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    v = l < int(blockDim.x >> 5) ? scratch[l] : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (l == 0) scratch[0] = v;
-  }
-  __syncthreads();
-  v = scratch[0];
-  __syncthreads();
-  return v;
-}
-
-template <int DT, int FMT>
-__global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
-  extern __shared__ float prow[];  // n_t pressures, then 32 floats of scratch
-  float* scratch = prow + ((p.n_t + 31) & ~31);
-  const int s = blockIdx.x, f = blockIdx.y;
-  const int64_t r = int64_t(f) * p.n_sensors + s;
-  const float sc = p.scales ? p.scales[r] : 1.0f;
-  const int64_t src0 = r * p.n_t;
-  for (int k = threadIdx.x; k < p.n_t; k += blockDim.x) prow[k] = load_sample<DT>(p.sig, src0 + k) * sc;
-  __syncthreads();
-  const float w = p.weights[s];
-  const int64_t dst0 = r * p.n_t_pad;
-  if constexpr (FMT == kBF32) {
-    float* b = static_cast<float*>(p.b) + dst0;
-    for (int k = threadIdx.x; k < p.n_t_pad; k += blockDim.x) b[k] = integrand(prow, k, p.n_t);
-    if (threadIdx.x == 0) p.m[int64_t(f) * p.n_sensors_pad + s] = w;
+template <int FMT>
+__device__ __forceinline__ uint32_t encode_pair(float v0, float v1) {
+  if constexpr (FMT == kBBF16P) {
+    const __nv_bfloat16 q0 = __float2bfloat16_rn(v0);
+    const __nv_bfloat16 q1 = __float2bfloat16_rn(v1 - __bfloat162float(q0));
+    return uint32_t(__bfloat16_as_ushort(q0)) | (uint32_t(__bfloat16_as_ushort(q1)) << 16);
   } else {
-    float mx = 0.0f;
-    for (int k = threadIdx.x; k < p.n_t; k += blockDim.x) mx = fmaxf(mx, fabsf(integrand(prow, k, p.n_t)));
-    mx = block_max(mx, scratch);
-    const float sigma = mx > 0.0f ? mx : 1.0f;
-    const float inv = 1.0f / sigma;
-    uint32_t* b = static_cast<uint32_t*>(p.b) + dst0;
-    for (int k = threadIdx.x; k < p.n_t_pad; k += blockDim.x) {
-      const float v0 = integrand(prow, k, p.n_t) * inv;
-      const float v1 = integrand(prow, k + 1, p.n_t) * inv;
-      uint32_t word;
-      if constexpr (FMT == kBBF16P) {
-        const __nv_bfloat16 q0 = __float2bfloat16_rn(v0);
-        const __nv_bfloat16 q1 = __float2bfloat16_rn(v1 - __bfloat162float(q0));
-        word = uint32_t(__bfloat16_as_ushort(q0)) | (uint32_t(__bfloat16_as_ushort(q1)) << 16);
-      } else {
-        const __half q0 = __float2half_rn(v0);
-        const __half q1 = __float2half_rn(v1 - __half2float(q0));
-        word = uint32_t(__half_as_ushort(q0)) | (uint32_t(__half_as_ushort(q1)) << 16);
-      }
-      b[k] = word;
+    const __half q0 = __float2half_rn(v0);
+    const __half q1 = __float2half_rn(v1 - __half2float(q0));
+    return uint32_t(__half_as_ushort(q0)) | (uint32_t(__half_as_ushort(q1)) << 16);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_words(uint32_t* dst, const uint32_t (&w)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 4)
+      *reinterpret_cast<uint4*>(dst + i) = make_uint4(w[i], w[i + 1], w[i + 2], w[i + 3]);
+  } else if constexpr (N == 2) {
+    *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+  } else {
+    dst[0] = w[0];
+  }
+}
+
+// One CTA per (sensor, frame group): FB frame-interleaved integrand rows.
+template <int DT, int FMT, int FB>
+__global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
+  __shared__ float red[8][FB];
+  const int s = blockIdx.x, g = blockIdx.y;
+  const int f0 = g * FB;
+  const int fb_eff = min(FB, p.n_frames - f0);
+  const int n = p.n_t;
+  int64_t row0[FB];
+  float sc[FB];
+#pragma unroll
+  for (int fb = 0; fb < FB; ++fb) {
+    const int f = min(f0 + fb, p.n_frames - 1);
+    const int64_t r = int64_t(f) * p.n_sensors + s;
+    row0[fb] = r * n;
+    sc[fb] = p.scales ? p.scales[r] : 1.0f;
+  }
+  float inv[FB], sigma[FB];
+#pragma unroll
+  for (int fb = 0; fb < FB; ++fb) sigma[fb] = inv[fb] = 1.0f;
+  if constexpr (FMT != kBF32) {
+    float mx[FB];
+#pragma unroll
+    for (int fb = 0; fb < FB; ++fb) mx[fb] = 0.0f;
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb) mx[fb] = fmaxf(mx[fb], fabsf(integrand<DT>(p.sig, row0[fb], sc[fb], k, n)));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int fb = 0; fb < FB; ++fb) {
+      float v = mx[fb];
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (l == 0) red[w][fb] = v;
     }
-    if (threadIdx.x == 0) p.m[int64_t(f) * p.n_sensors_pad + s] = w * sigma;
+    __syncthreads();
+#pragma unroll
+    for (int fb = 0; fb < FB; ++fb) {
+      float v = 0.0f;
+      for (int q = 0; q < int(blockDim.x >> 5); ++q) v = fmaxf(v, red[q][fb]);
+      sigma[fb] = v > 0.0f ? v : 1.0f;
+      inv[fb] = 1.0f / sigma[fb];
+    }
+  }
+  uint32_t* dst = static_cast<uint32_t*>(p.b) + (int64_t(g) * p.n_sensors + s) * p.n_t_pad * FB;
+  for (int k = threadIdx.x; k < p.n_t_pad; k += blockDim.x) {
+    uint32_t wds[FB];
+#pragma unroll
+    for (int fb = 0; fb < FB; ++fb) {
+      if (fb < fb_eff) {
+        if constexpr (FMT == kBF32) {
+          wds[fb] = __float_as_uint(integrand<DT>(p.sig, row0[fb], sc[fb], k, n));
+        } else {
+          const float v0 = integrand<DT>(p.sig, row0[fb], sc[fb], k, n) * inv[fb];
+          const float v1 = integrand<DT>(p.sig, row0[fb], sc[fb], k + 1, n) * inv[fb];
+          wds[fb] = encode_pair<FMT>(v0, v1);
+        }
+      } else {
+        wds[fb] = 0u;
+      }
+    }
+    store_words<FB>(dst + int64_t(k) * FB, wds);
+  }
+  if (threadIdx.x < FB) {
+    const int fb = threadIdx.x;
+    float mval = 0.0f;
+#pragma unroll
+    for (int q = 0; q < FB; ++q)
+      if (q == fb && fb < fb_eff) mval = p.weights[s] * sigma[q];
+    p.m[(int64_t(g) * p.n_sensors_pad + s) * FB + fb] = mval;
   }
 }
 
 // ------------------------------------------------------------------ gather --
-template <int FMT>
-__device__ __forceinline__ float lerp_window(const unsigned char* wrow, unsigned i, float ph) {
-  if constexpr (FMT == kBF32) {
-    const float* b = reinterpret_cast<const float*>(wrow);
-    const float b0 = b[i], b1 = b[i + 1];
-    return fmaf(ph, b1 - b0, b0);
-  } else if constexpr (FMT == kBBF16P) {
-    const uint32_t wd = reinterpret_cast<const uint32_t*>(wrow)[i];
-    return fmaf(ph, __uint_as_float(wd & 0xffff0000u), __uint_as_float(wd << 16));
+template <int N>
+__device__ __forceinline__ void load_words(const uint32_t* src, uint32_t (&w)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 4) {
+      const uint4 v = *reinterpret_cast<const uint4*>(src + i);
+      w[i] = v.x; w[i + 1] = v.y; w[i + 2] = v.z; w[i + 3] = v.w;
+    }
+  } else if constexpr (N == 2) {
+    const uint2 v = *reinterpret_cast<const uint2*>(src);
+    w[0] = v.x; w[1] = v.y;
   } else {
-    const uint32_t wd = reinterpret_cast<const uint32_t*>(wrow)[i];
-    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&wd));
-    return fmaf(ph, v.y, v.x);
+    w[0] = src[0];
   }
 }
 
-constexpr int kMaxStages = 8;
-constexpr int kMaxS = 32;
+// One sensor of a stage for this lane's 4 pixels and FB frames.
+template <int P, int FB, int FMT>
+__device__ __forceinline__ void gather_sensor(float (&acc)[FB][4], const float* su, const uint32_t* sm,
+                                              const int* soff, const uint32_t* sw, int sl, int Wst) {
+  const int off = soff[sl];
+  const unsigned lim = unsigned(Wst - off);
+  float mm[FB];
+  {
+    uint32_t mw[FB];
+    load_words<FB>(sm + sl * FB, mw);
+#pragma unroll
+    for (int fb = 0; fb < FB; ++fb) mm[fb] = __uint_as_float(mw[fb]);
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const float uu = su[sl * P + x * 32];
+    const unsigned i = min(unsigned(__float2int_rz(uu)), lim);
+    const float ph = uu - float(i);
+    const uint32_t* row = sw + size_t(i + unsigned(off)) * FB;
+    uint32_t w0[FB];
+    load_words<FB>(row, w0);
+    if constexpr (FMT == kBF32) {
+      uint32_t w1[FB];
+      load_words<FB>(row + FB, w1);
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb) {
+        const float b0 = __uint_as_float(w0[fb]), b1 = __uint_as_float(w1[fb]);
+        acc[fb][x] = fmaf(mm[fb], fmaf(ph, b1 - b0, b0), acc[fb][x]);
+      }
+    } else if constexpr (FMT == kBBF16P) {
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb) {
+        const float v = fmaf(ph, __uint_as_float(w0[fb] & 0xffff0000u), __uint_as_float(w0[fb] << 16));
+        acc[fb][x] = fmaf(mm[fb], v, acc[fb][x]);
+      }
+    } else {
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb) {
+        const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&w0[fb]));
+        acc[fb][x] = fmaf(mm[fb], fmaf(ph, h.y, h.x), acc[fb][x]);
+      }
+    }
+  }
+}
 
 // Shared-memory layout of one pipeline stage (byte offsets):
-//   u      [S][P] float           the tile's table rows of the stage's sensors
-//   m      [FB][S4] float         multipliers w_s * sigma per frame
-//   off    [S] int                window offset of each sensor inside a frame region
-//   win    [FB][Wst + 4] entries  the stage's windows packed at `off`, then 4
-//                                 zero entries that out-of-record pixels read
+//   u    [S][P] float            the tile's table rows of the stage's sensors
+//   m    [S4][FB] float          multipliers w_s * sigma
+//   off  [S4] int                window offset (rows) of each sensor
+//   win  [Wst + 4][FB] words     the stage's windows packed at `off`, then 4
+//                                zero rows that out-of-record pixels read
 struct StageLayout {
   size_t u, m, off, win, bytes;
   __host__ __device__ StageLayout(int S, int P, int FB, int Wst) {
     const int S4 = (S + 3) & ~3;
     u = 0;
     m = u + size_t(S) * P * 4;
-    off = m + size_t(FB) * S4 * 4;
-    win = off + size_t(((S + 3) & ~3)) * 4;
-    bytes = win + size_t(FB) * (Wst + 4) * 4;
+    off = m + size_t(S4) * FB * 4;
+    win = off + size_t(S4) * 4;
+    bytes = win + size_t(Wst + 4) * FB * 4;
   }
 };
 
+constexpr int kHeaderBytes = 256;   // mbarriers and flags
+constexpr int kMetaBytes = 2 * kMaxG * 4;
+
+struct UnitPos {
+  int inst, fg, tile, seg, s_lo, s_hi;
+};
+
+__device__ __forceinline__ UnitPos decode_unit(const StreamParams& p, int64_t u, int& inst) {
+  while (inst + 1 < p.n_inst && u >= p.inst[inst + 1].unit_begin) ++inst;
+  const InstDesc& d = p.inst[inst];
+  const int64_t loc = u - d.unit_begin;
+  const int64_t per_fg = int64_t(d.n_tiles) * d.n_seg;
+  UnitPos q;
+  q.inst = inst;
+  q.fg = int(loc / per_fg);
+  const int64_t r = loc - int64_t(q.fg) * per_fg;
+  q.tile = int(r / d.n_seg);
+  q.seg = int(r - int64_t(q.tile) * d.n_seg);
+  q.s_lo = q.seg * d.G;
+  q.s_hi = min(d.n_sensors, q.s_lo + d.G);
+  return q;
+}
+
 template <int P, int FB, int FMT, int SW>
-__global__ void __launch_bounds__(32 * ((P / 128) * SW + 1)) gather_kernel(const GatherParams p) {
-  constexpr int PW = P / 128;       // warps across the tile's pixels
-  constexpr int NWC = PW * SW;      // consumer warps
+__global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
+    gather_kernel(const __grid_constant__ StreamParams p) {
+  constexpr int PW = P / 128;   // warps across the tile's pixels
+  constexpr int NWC = PW * SW;  // consumer warps
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + kMaxStages;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kMaxStages);
+  uint64_t* meta_bar = empty + kMaxStages;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(meta_bar + 2);
+  int* meta = reinterpret_cast<int*>(smem + kHeaderBytes);  // [2][kMaxG] packed bases
+  const StageLayout L(p.S, P, FB, p.Wst);
+  unsigned char* stage0 = smem + kHeaderBytes + kMetaBytes;
+  float* red = reinterpret_cast<float*>(stage0 + L.bytes * p.stages);  // [2][SW][FB][P]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, rank = blockIdx.y;
-  const int f0 = blockIdx.z * FB;
-  const int fb_eff = min(FB, p.n_frames - f0);
-  const int s_begin = rank * p.split_len;
-  const int s_end = min(p.n_sensors, s_begin + p.split_len);
-  const int n_chunks = s_end > s_begin ? (s_end - s_begin + p.S - 1) / p.S : 0;
+  const int64_t ua = int64_t(blockIdx.x) * p.n_units / gridDim.x;
+  const int64_t ub = int64_t(blockIdx.x + 1) * p.n_units / gridDim.x;
   const int S4 = (p.S + 3) & ~3;
-  const int pitch = p.Wst + 4;  // entries per frame region of a stage
-  const StageLayout L(p.S, P, FB, p.Wst);
-  unsigned char* stage0 = smem + 256;
-  float* red = reinterpret_cast<float*>(stage0 + L.bytes * p.stages);  // [SW][FB][P]
-  float* fin = red + SW * FB * P;                                      // [FB][P]
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < p.stages; ++st) {
       mbar_init(&full[st], 1);
       mbar_init(&empty[st], NWC);
     }
+    mbar_init(&meta_bar[0], 1);
+    mbar_init(&meta_bar[1], 1);
     *abort_flag = 0;
     mbar_init_fence();
   }
-  // the 4 zero entries after every frame region of every stage
-  for (int q = threadIdx.x; q < p.stages * FB * 4; q += blockDim.x) {
-    const int st = q / (FB * 4), rem = q - st * FB * 4;
-    const int fb = rem >> 2, k = rem & 3;
-    reinterpret_cast<uint32_t*>(stage0 + st * L.bytes + L.win)[size_t(fb) * pitch + p.Wst + k] = 0u;
+  // zero rows after the windows of every stage
+  for (int q = threadIdx.x; q < p.stages * 4 * FB; q += blockDim.x) {
+    const int st = q / (4 * FB), k = q - st * 4 * FB;
+    reinterpret_cast<uint32_t*>(stage0 + st * L.bytes + L.win)[size_t(p.Wst) * FB + k] = 0u;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
 
   if (warp == NWC) {
     // ------------------------------------------------------------ producer --
-    int issued = 0;
-    for (int c = 0; c < n_chunks; ++c) {
-      const int st = c % p.stages, use = c / p.stages;
-      if (use > 0 && !mbar_wait_bounded(&empty[st], (use - 1) & 1, p.timeout_ns, abort_flag)) {
+    int inst = 0;
+    int64_t seq = 0;         // chunks issued by this CTA
+    int64_t meta_last = -1;  // last unit whose bases were requested
+    auto issue_meta = [&](int64_t u, int slot) {
+      meta_last = u;
+      int ii = inst;
+      const UnitPos q = decode_unit(p, u, ii);
+      const InstDesc& d = p.inst[q.inst];
+      const uint32_t n4 = uint32_t((q.s_hi - q.s_lo + 3) & ~3);
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&meta_bar[slot], n4 * 4);
+        bulk_g2s(meta + slot * kMaxG, d.base + int64_t(q.tile) * d.n_sensors_pad + q.s_lo, n4 * 4,
+                 &meta_bar[slot]);
+      }
+    };
+    bool ok = true;
+    if (ua < ub) issue_meta(ua, 0);
+    for (int64_t u = ua; u < ub && ok; ++u) {
+      const int64_t k = u - ua;
+      const int slot = int(k & 1);
+      const UnitPos q = decode_unit(p, u, inst);
+      const InstDesc& d = p.inst[q.inst];
+      if (!mbar_wait_bounded(&meta_bar[slot], uint32_t((k >> 1) & 1), p.timeout_ns, abort_flag)) {
         if (lane == 0) {
           atomicOr(p.status, kStatusTimeout);
           *abort_flag = 1;
         }
         break;
       }
-      const int s0 = s_begin + c * p.S;
-      const int se = min(p.S, s_end - s0);
-      const int se4 = (se + 3) & ~3;
-      unsigned char* sb = stage0 + st * L.bytes;
-      // this lane's sensor (S <= 32): packed window base and length
-      int bs = 0, wl = 0;
-      if (lane < se) {
-        const uint32_t word = uint32_t(__ldg(p.base + size_t(tile) * p.n_sensors + s0 + lane));
-        bs = int(word & 0xffffu);
-        wl = int(word >> 16);
-      }
-      // exclusive prefix sum of the window lengths = packed offsets
-      int incl = wl;
+      __syncwarp();
+      if (u + 1 < ub) issue_meta(u + 1, slot ^ 1);
+      const int* mrow = meta + slot * kMaxG;
+      for (int s0 = q.s_lo; s0 < q.s_hi; s0 += p.S, ++seq) {
+        const int st = int(seq % p.stages);
+        const int64_t use = seq / p.stages;
+        if (use > 0 && !mbar_wait_bounded(&empty[st], uint32_t((use - 1) & 1), p.timeout_ns, abort_flag)) {
+          if (lane == 0) {
+            atomicOr(p.status, kStatusTimeout);
+            *abort_flag = 1;
+          }
+          ok = false;
+          break;
+        }
+        const int se = min(p.S, q.s_hi - s0);
+        const int se4 = (se + 3) & ~3;
+        unsigned char* sb = stage0 + st * L.bytes;
+        int bs = 0, wl = 0;
+        if (lane < se) {
+          const uint32_t word = uint32_t(mrow[s0 - q.s_lo + lane]);
+          bs = int(word & 0xffffu);
+          wl = int(word >> 16);
+        }
+        int incl = wl;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int total_w = __shfl_sync(0xffffffffu, incl, 31);
-      int off = incl - wl;
-      if (total_w > p.Wst) {  // cannot happen with a host-computed Wst; stay in bounds
-        if (lane == 0) atomicOr(p.status, kStatusBadConfig);
-        wl = 0;
-        off = 0;
-      }
-      const uint32_t wbytes = total_w > p.Wst ? 0u : uint32_t(total_w) * 4u;
-      if (lane < se) reinterpret_cast<int*>(sb + L.off)[lane] = off;
-      __syncwarp();
-      const uint32_t bytes = uint32_t(se) * P * 4 + uint32_t(fb_eff) * (se4 * 4 + wbytes);
-      if (lane == 0) mbar_arrive_expect_tx(&full[st], bytes);
-      __syncwarp();
-      if (lane == 0)
-        bulk_g2s(sb + L.u, p.u + (size_t(tile) * p.n_sensors + s0) * P, uint32_t(se) * P * 4,
-                 &full[st]);
-      if (lane < fb_eff)
-        bulk_g2s(sb + L.m + size_t(lane) * S4 * 4,
-                 p.m + size_t(f0 + lane) * p.n_sensors_pad + s0, uint32_t(se4) * 4, &full[st]);
-      if (wl > 0) {
-        for (int fb = 0; fb < fb_eff; ++fb) {
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int total_w = __shfl_sync(0xffffffffu, incl, 31);
+        int off = incl - wl;
+        uint32_t wrows = uint32_t(total_w);
+        if (total_w > p.Wst) {  // cannot happen with a host-computed Wst; stay in bounds
+          if (lane == 0) atomicOr(p.status, kStatusBadConfig);
+          wl = 0;
+          off = 0;
+          wrows = 0;
+        }
+        if (lane < S4) reinterpret_cast<int*>(sb + L.off)[lane] = lane < se ? off : 0;
+        __syncwarp();
+        const uint32_t bytes = uint32_t(se) * P * 4 + uint32_t(se4) * FB * 4 + wrows * FB * 4;
+        if (lane == 0) mbar_arrive_expect_tx(&full[st], bytes);
+        __syncwarp();
+        if (lane == 0) {
+          bulk_g2s(sb + L.u, d.u + (int64_t(q.tile) * d.n_sensors + s0) * P, uint32_t(se) * P * 4,
+                   &full[st]);
+          bulk_g2s(sb + L.m, d.m + (int64_t(q.fg) * d.n_sensors_pad + s0) * FB,
+                   uint32_t(se4) * FB * 4, &full[st]);
+        }
+        if (wl > 0) {
           const unsigned char* src =
-              static_cast<const unsigned char*>(p.b) +
-              ((size_t(f0 + fb) * p.n_sensors + s0 + lane) * p.n_t_pad + bs) * 4;
-          bulk_g2s(sb + L.win + (size_t(fb) * pitch + off) * 4, src, uint32_t(wl) * 4, &full[st]);
+              static_cast<const unsigned char*>(d.b) +
+              ((int64_t(q.fg) * d.n_sensors + s0 + lane) * d.n_t_pad + bs) * (FB * 4);
+          bulk_g2s(sb + L.win + size_t(off) * FB * 4, src, uint32_t(wl) * FB * 4, &full[st]);
         }
       }
-      issued = c + 1;
     }
     // drain the copies still in flight before the CTA may exit
-    for (int c = max(0, issued - p.stages); c < issued; ++c)
-      mbar_wait_bounded(&full[c % p.stages], (c / p.stages) & 1, p.timeout_ns, nullptr);
-  } else {
+    for (int64_t c = seq > p.stages ? seq - p.stages : 0; c < seq; ++c)
+      mbar_wait_bounded(&full[c % p.stages], uint32_t((c / p.stages) & 1), p.timeout_ns, nullptr);
+    if (meta_last >= 0) {
+      // the last base copy (one unit ahead) may still be in flight after an abort
+      const int64_t k = meta_last - ua;
+      mbar_wait_bounded(&meta_bar[k & 1], uint32_t((k >> 1) & 1), p.timeout_ns, nullptr);
+    }
+  } else if (warp < NWC) {
     // ------------------------------------------------------------ consumers --
     const int pg = warp % PW, sp = warp / PW;
-    if (rank == 0 && p.n_zero_runs > 0) {
-      for (int fb = 0; fb < fb_eff; ++fb) {
-        float* o = p.out + int64_t(f0 + fb) * p.out_stride;
-        for (int r = tile + p.n_tiles * warp; r < p.n_zero_runs; r += p.n_tiles * NWC) {
-          const int st0 = p.zero_runs[2 * r], len = p.zero_runs[2 * r + 1];
-          for (int i = lane; i < len; i += 32) o[st0 + i] = 0.0f;
-        }
-      }
-    }
-    float acc[FB][4];
+    int inst = 0;
+    int64_t seq = 0;
+    bool ok = true;
+    for (int64_t u = ua; u < ub; ++u) {
+      const UnitPos q = decode_unit(p, u, inst);
+      const int64_t j = u - ua;
+      float acc[FB][4];
 #pragma unroll
-    for (int fb = 0; fb < FB; ++fb)
+      for (int fb = 0; fb < FB; ++fb)
 #pragma unroll
-      for (int x = 0; x < 4; ++x) acc[fb][x] = 0.0f;
-    for (int c = 0; c < n_chunks; ++c) {
-      const int st = c % p.stages;
-      if (!mbar_wait_bounded(&full[st], (c / p.stages) & 1, p.timeout_ns, abort_flag)) {
-        if (lane == 0) {
-          atomicOr(p.status, kStatusTimeout);
-          *abort_flag = 1;
-        }
-        break;
-      }
-      const int se = min(p.S, s_end - (s_begin + c * p.S));
-      const unsigned char* sb = stage0 + st * L.bytes;
-      const float* su = reinterpret_cast<const float*>(sb + L.u) + pg * 128 + lane;
-      const float* sm = reinterpret_cast<const float*>(sb + L.m);
-      const int* soff = reinterpret_cast<const int*>(sb + L.off);
-      const unsigned char* sw = sb + L.win;
-      for (int sl = sp; sl < se; sl += SW) {
-        const int off = soff[sl];
-        const unsigned lim = unsigned(p.Wst - off);
-        unsigned ii[4];
-        float ph[4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          const float uu = su[sl * P + x * 32];
-          const unsigned i = min(unsigned(__float2int_rz(uu)), lim);
-          ph[x] = uu - float(i);
-          ii[x] = i + unsigned(off);
-        }
-#pragma unroll
-        for (int fb = 0; fb < FB; ++fb) {
-          if (fb < fb_eff) {
-            const float mm = sm[fb * S4 + sl];
-            const unsigned char* wrow = sw + size_t(fb) * pitch * 4;
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-              acc[fb][x] = fmaf(mm, lerp_window<FMT>(wrow, ii[x], ph[x]), acc[fb][x]);
+        for (int x = 0; x < 4; ++x) acc[fb][x] = 0.0f;
+      for (int s0 = q.s_lo; s0 < q.s_hi; s0 += p.S, ++seq) {
+        if (!ok) continue;  // after an abort: keep the epilogue hand-off going, compute nothing
+        const int st = int(seq % p.stages);
+        if (!mbar_wait_bounded(&full[st], uint32_t((seq / p.stages) & 1), p.timeout_ns, abort_flag)) {
+          if (lane == 0) {
+            atomicOr(p.status, kStatusTimeout);
+            *abort_flag = 1;
           }
+          ok = false;
+          continue;
         }
+        const int se = min(p.S, q.s_hi - s0);
+        const unsigned char* sb = stage0 + st * L.bytes;
+        const float* su = reinterpret_cast<const float*>(sb + L.u) + pg * 128 + lane;
+        const uint32_t* sm = reinterpret_cast<const uint32_t*>(sb + L.m);
+        const int* soff = reinterpret_cast<const int*>(sb + L.off);
+        const uint32_t* sw = reinterpret_cast<const uint32_t*>(sb + L.win);
+        int sl = sp;
+        for (; sl + SW < se; sl += 2 * SW) {
+          gather_sensor<P, FB, FMT>(acc, su, sm, soff, sw, sl, p.Wst);
+          gather_sensor<P, FB, FMT>(acc, su, sm, soff, sw, sl + SW, p.Wst);
+        }
+        if (sl < se) gather_sensor<P, FB, FMT>(acc, su, sm, soff, sw, sl, p.Wst);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+      }
+      // hand the unit's sums to the epilogue warp through red[j & 1]
+      const int buf = int(j & 1);
+      if (j >= 2) red_free_sync(buf, (NWC + 1) * 32);
+      float* rb = red + size_t(buf) * SW * FB * P;
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) rb[(sp * FB + fb) * P + pg * 128 + x * 32 + lane] = acc[fb][x];
+      red_full_arrive(buf, (NWC + 1) * 32);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogues --
+    // Two epilogue warps take alternate units (ew = unit parity = red buffer).
+    const int ew = warp - NWC - 1;
+    for (int i = 0; i < p.n_inst; ++i) {
+      const InstDesc& d = p.inst[i];
+      for (int f = 0; f < d.n_frames && d.n_zero_runs > 0; ++f)
+        for (int64_t r = int64_t(blockIdx.x) * 2 + ew; r < d.n_zero_runs; r += int64_t(gridDim.x) * 2) {
+          const int st0 = d.zero_runs[2 * r], len = d.zero_runs[2 * r + 1];
+          float* o = d.out + int64_t(f) * d.out_stride + st0;
+          for (int i2 = lane; i2 < len; i2 += 32) o[i2] = 0.0f;
+        }
+    }
+    constexpr int KO = P / 32;  // outputs of one frame per lane
+    int inst = 0;
+    for (int64_t u = ua + ew; u < ub; u += 2) {
+      const UnitPos q = decode_unit(p, u, inst);
+      const InstDesc& d = p.inst[q.inst];
+      const int buf = ew;
+      const int f0 = q.fg * FB;
+      const int fb_eff = min(FB, d.n_frames - f0);
+      int slot_idx[KO];
+#pragma unroll
+      for (int k = 0; k < KO; ++k) slot_idx[k] = __ldg(d.slot + int64_t(q.tile) * P + k * 32 + lane);
+      red_full_sync(buf, (NWC + 1) * 32);
+      const float* rb = red + size_t(buf) * SW * FB * P;
+      const int64_t pbase = ((int64_t(q.fg) * d.n_tiles + q.tile) * d.n_seg) * FB * P;
+      float v[FB][KO];
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb)
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+          const int o = fb * P + k * 32 + lane;
+          float a = 0.0f;
+#pragma unroll
+          for (int ph = 0; ph < SW; ++ph) a += rb[ph * FB * P + o];  // fixed phase order
+          v[fb][k] = a;
+        }
+      if (u + 2 < ub) red_free_arrive(buf, (NWC + 1) * 32);  // red[buf] free again
+      if (d.n_seg == 1) {
+#pragma unroll
+        for (int fb = 0; fb < FB; ++fb)
+#pragma unroll
+          for (int k = 0; k < KO; ++k)
+            if (fb < fb_eff && slot_idx[k] >= 0) d.out[int64_t(f0 + fb) * d.out_stride + slot_idx[k]] = v[fb][k];
+        continue;
+      }
+      float* mine = d.part + pbase + int64_t(q.seg) * FB * P;
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb)
+#pragma unroll
+        for (int k = 0; k < KO; ++k) __stcg(mine + fb * P + k * 32 + lane, v[fb][k]);
+      // the last segment of a tile to finish sums all segments in fixed order
+      __threadfence();
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) last = atomicAdd(d.counter + int64_t(q.fg) * d.n_tiles + q.tile, 1) == d.n_seg - 1;
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (!last) continue;
+      __threadfence();
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb) {
+        if (fb >= fb_eff) break;
+        float t[KO];
+#pragma unroll
+        for (int k = 0; k < KO; ++k) t[k] = 0.0f;
+        for (int sg = 0; sg < d.n_seg; ++sg) {
+          const float* src = d.part + pbase + int64_t(sg) * FB * P + fb * P + lane;
+          float x[KO];
+#pragma unroll
+          for (int k = 0; k < KO; ++k) x[k] = __ldcg(src + k * 32);
+#pragma unroll
+          for (int k = 0; k < KO; ++k) t[k] += x[k];
+        }
+#pragma unroll
+        for (int k = 0; k < KO; ++k)
+          if (slot_idx[k] >= 0) d.out[int64_t(f0 + fb) * d.out_stride + slot_idx[k]] = t[k];
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);
+      if (lane == 0) atomicExch(d.counter + int64_t(q.fg) * d.n_tiles + q.tile, 0);
     }
-    // fixed-order sum of the sensor phases
-#pragma unroll
-    for (int fb = 0; fb < FB; ++fb)
-#pragma unroll
-      for (int x = 0; x < 4; ++x) red[(sp * FB + fb) * P + pg * 128 + x * 32 + lane] = acc[fb][x];
-    named_barrier(1, NWC * 32);
-    for (int o = threadIdx.x; o < FB * P; o += NWC * 32) {
-      float v = 0.0f;
-#pragma unroll
-      for (int q = 0; q < SW; ++q) v += red[q * FB * P + o];
-      if (p.split == 1) {
-        const int fb = o / P, pp = o - fb * P;
-        if (fb < fb_eff) {
-          const int idx = p.slot[size_t(tile) * P + pp];
-          if (idx >= 0) p.out[int64_t(f0 + fb) * p.out_stride + idx] = v;
-        }
-      } else {
-        fin[o] = v;
-      }
-    }
-  }
-
-  if (p.split > 1) {
-    // fixed-order sum of the cluster ranks (sensor splits) through DSMEM
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
-    if (warp < NWC) {
-      const int total = FB * P;
-      const int chunk = (total + p.split - 1) / p.split;
-      const int o_end = min(total, (rank + 1) * chunk);
-      for (int o = rank * chunk + threadIdx.x; o < o_end; o += NWC * 32) {
-        float v = 0.0f;
-        for (int q = 0; q < p.split; ++q) v += cl.map_shared_rank(fin, q)[o];
-        const int fb = o / P, pp = o - fb * P;
-        if (fb < fb_eff) {
-          const int idx = p.slot[size_t(tile) * P + pp];
-          if (idx >= 0) p.out[int64_t(f0 + fb) * p.out_stride + idx] = v;
-        }
-      }
-    }
-    cl.sync();
   }
 }
 
@@ -442,87 +638,99 @@ __global__ void wait_probe_kernel(int* status, uint64_t timeout_ns) {
 }
 
 // --------------------------------------------------------------- launchers --
-int gather_threads(const GatherConfig& c) { return 32 * ((c.P / 128) * c.SW + 1); }
+int gather_threads(const GatherConfig& c) { return 32 * ((c.P / 128) * c.SW + 3); }
 
-size_t gather_smem_bytes(const GatherConfig& c, int fmt, int Wst) {
-  (void)fmt;
+size_t gather_smem_bytes(const GatherConfig& c, int Wst) {
   const StageLayout L(c.S, c.P, c.FB, Wst);
-  return 256 + L.bytes * c.stages + size_t(c.SW) * c.FB * c.P * 4 + size_t(c.FB) * c.P * 4;
+  return size_t(kHeaderBytes) + kMetaBytes + L.bytes * c.stages + 2 * size_t(c.SW) * c.FB * c.P * 4;
 }
 
-cudaError_t launch_preprocess(const PreParams& p, cudaStream_t st) {
-  const size_t smem = (size_t((p.n_t + 31) & ~31) + 32) * sizeof(float);
-  dim3 grid(p.n_sensors, p.n_frames);
-  void (*kern)(const PreParams) = nullptr;
-#define PAT_PRE_CASE(DT, FMT) \
-  if (p.dtype == DT && p.fmt == FMT) kern = preprocess_kernel<DT, FMT>;
-  PAT_PRE_CASE(0, kBF32)
-  PAT_PRE_CASE(0, kBBF16P)
-  PAT_PRE_CASE(0, kBF16P)
-  PAT_PRE_CASE(1, kBF32)
-  PAT_PRE_CASE(1, kBBF16P)
-  PAT_PRE_CASE(1, kBF16P)
-  PAT_PRE_CASE(2, kBF32)
-  PAT_PRE_CASE(2, kBBF16P)
-  PAT_PRE_CASE(2, kBF16P)
-#undef PAT_PRE_CASE
-  if (!kern) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  kern<<<grid, 256, smem, st>>>(p);
+template <int DT, int FMT>
+static cudaError_t launch_pre_fb(const PreParams& p, cudaStream_t st) {
+  dim3 grid(p.n_sensors, (p.n_frames + p.FB - 1) / p.FB);
+  switch (p.FB) {
+    case 1: preprocess_kernel<DT, FMT, 1><<<grid, 256, 0, st>>>(p); break;
+    case 2: preprocess_kernel<DT, FMT, 2><<<grid, 256, 0, st>>>(p); break;
+    case 4: preprocess_kernel<DT, FMT, 4><<<grid, 256, 0, st>>>(p); break;
+    case 8: preprocess_kernel<DT, FMT, 8><<<grid, 256, 0, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
+cudaError_t launch_preprocess(const PreParams& p, cudaStream_t st) {
+  if (p.dtype == 0 && p.fmt == kBF32) return launch_pre_fb<0, kBF32>(p, st);
+  if (p.dtype == 1 && p.fmt == kBBF16P) return launch_pre_fb<1, kBBF16P>(p, st);
+  if (p.dtype == 2 && p.fmt == kBF16P) return launch_pre_fb<2, kBF16P>(p, st);
+  return cudaErrorInvalidValue;
+}
+
 template <int P, int FB, int FMT, int SW>
-static cudaError_t launch_gather_t(const GatherParams& p, size_t smem, cudaStream_t st) {
+static cudaError_t gather_t(const StreamParams& p, size_t smem, int grid, cudaStream_t st,
+                            int* resident, int n_sm) {
   auto kern = gather_kernel<P, FB, FMT, SW>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(p.n_tiles, p.split, (p.n_frames + FB - 1) / FB);
-  cfg.blockDim = dim3(32 * ((P / 128) * SW + 1));
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  int na = 0;
-  if (p.split > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = p.split;
-    attr[0].val.clusterDim.z = 1;
-    na = 1;
+  static size_t smem_set = 0;  // largest dynamic smem granted so far (per instantiation)
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
   }
-  cfg.attrs = attr;
-  cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, kern, p);
+  const int threads = 32 * ((P / 128) * SW + 3);
+  if (resident) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    *resident = per_sm * n_sm;
+    return cudaSuccess;
+  }
+  kern<<<grid, threads, smem, st>>>(p);
+  return cudaGetLastError();
 }
 
 template <int P, int FMT, int SW>
-static cudaError_t launch_gather_fb(int FB, const GatherParams& p, size_t smem, cudaStream_t st) {
+static cudaError_t gather_fb(int FB, const StreamParams& p, size_t smem, int grid, cudaStream_t st,
+                             int* resident, int n_sm) {
   switch (FB) {
-    case 1: return launch_gather_t<P, 1, FMT, SW>(p, smem, st);
-    case 2: return launch_gather_t<P, 2, FMT, SW>(p, smem, st);
-    case 4: return launch_gather_t<P, 4, FMT, SW>(p, smem, st);
-    case 8: return launch_gather_t<P, 8, FMT, SW>(p, smem, st);
+    case 1: return gather_t<P, 1, FMT, SW>(p, smem, grid, st, resident, n_sm);
+    case 2: return gather_t<P, 2, FMT, SW>(p, smem, grid, st, resident, n_sm);
+    case 4: return gather_t<P, 4, FMT, SW>(p, smem, grid, st, resident, n_sm);
+    case 8: return gather_t<P, 8, FMT, SW>(p, smem, grid, st, resident, n_sm);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_gather(const GatherConfig& c, int fmt, const GatherParams& p, cudaStream_t st) {
-  if (p.stages < 1 || p.stages > kMaxStages || p.S % 4 || p.S % c.SW || p.S > kMaxS ||
-      p.split < 1 || p.split > 8 || p.split_len % 4 || p.Wst % 8)
-    return cudaErrorInvalidValue;
-  const size_t smem = gather_smem_bytes(c, fmt, p.Wst);
+static cudaError_t gather_dispatch(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
+                                   cudaStream_t st, int* resident, int n_sm) {
+  const size_t smem = gather_smem_bytes(c, p.Wst);
   if (c.P == 128 && c.SW == 4) {
-    if (fmt == kBF32) return launch_gather_fb<128, kBF32, 4>(c.FB, p, smem, st);
-    if (fmt == kBBF16P) return launch_gather_fb<128, kBBF16P, 4>(c.FB, p, smem, st);
-    if (fmt == kBF16P) return launch_gather_fb<128, kBF16P, 4>(c.FB, p, smem, st);
+    if (fmt == kBF32) return gather_fb<128, kBF32, 4>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBBF16P) return gather_fb<128, kBBF16P, 4>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBF16P) return gather_fb<128, kBF16P, 4>(c.FB, p, smem, grid, st, resident, n_sm);
   } else if (c.P == 256 && c.SW == 2) {
-    if (fmt == kBF32) return launch_gather_fb<256, kBF32, 2>(c.FB, p, smem, st);
-    if (fmt == kBBF16P) return launch_gather_fb<256, kBBF16P, 2>(c.FB, p, smem, st);
-    if (fmt == kBF16P) return launch_gather_fb<256, kBF16P, 2>(c.FB, p, smem, st);
+    if (fmt == kBF32) return gather_fb<256, kBF32, 2>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBBF16P) return gather_fb<256, kBBF16P, 2>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBF16P) return gather_fb<256, kBF16P, 2>(c.FB, p, smem, grid, st, resident, n_sm);
   }
   return cudaErrorInvalidValue;
+}
+
+int gather_resident_ctas(const GatherConfig& c, int fmt, int Wst, int n_sm) {
+  StreamParams dummy;
+  dummy.Wst = Wst;
+  int resident = 0;
+  if (gather_dispatch(c, fmt, dummy, 0, nullptr, &resident, n_sm) != cudaSuccess) return 0;
+  return resident;
+}
+
+cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
+                          cudaStream_t st) {
+  if (p.stages < 1 || p.stages > kMaxStages || p.S % 4 || p.S % c.SW || p.S > kMaxS ||
+      p.Wst % 8 || p.n_inst < 1 || p.n_inst > kMaxInst || grid < 1)
+    return cudaErrorInvalidValue;
+  for (int i = 0; i < p.n_inst; ++i)
+    if (p.inst[i].G % p.S || p.inst[i].G > kMaxG || p.inst[i].Wst > p.Wst) return cudaErrorInvalidValue;
+  if (p.n_units == 0) return cudaSuccess;
+  return gather_dispatch(c, fmt, p, grid, st, nullptr, 0);
 }
 
 cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t st) {

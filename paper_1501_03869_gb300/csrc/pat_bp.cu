@@ -55,13 +55,16 @@ struct pat_bp_s {
   double dt = 0.0;
   unsigned flags = 0;
   bool compact = false;
-  int P = 128, SW = 4, n_tiles = 0, W = 0, split = 1, split_len = 0;
+  int P = 128, SW = 4, n_tiles = 0, W = 0;
+  int G = 64, n_seg = 1;              // sensors per segment, segments per tile
   int64_t n_pix = 0, grid_total = 0, out_stride = 0;
   int n_zero_runs = 0;
   double build_seconds = 0.0;
   std::vector<uint16_t> win_len;      // host copy of the window lengths [tile][sensor]
   int pre_frames = 0;                 // frames held by the integrand buffer
   int pre_fmt = 0;                    // their storage format
+  int pre_fb = 1;                     // their frames per group
+  int resident[4][3][2] = {};         // cached CTAs per launch by (FB index, format, S == 8)
   int wst_cache[33] = {0};            // stage window bound per sensors-per-stage
   float* d_u = nullptr;
   int32_t* d_base = nullptr;
@@ -73,6 +76,10 @@ struct pat_bp_s {
   size_t b_cap = 0;
   float* d_m = nullptr;
   size_t m_cap = 0;
+  float* d_part = nullptr;            // segment partial sums (scratch)
+  size_t part_cap = 0;
+  int* d_counter = nullptr;           // per (frame group, tile) segment counters
+  size_t counter_cap = 0;
   // staging of pat_bp_reconstruct_host
   cudaStream_t own_stream = nullptr;
   void* d_sig = nullptr;
@@ -136,6 +143,8 @@ static void free_handle(pat_bp_t h) {
   cudaFree(h->d_status);
   cudaFree(h->d_b);
   cudaFree(h->d_m);
+  cudaFree(h->d_part);
+  cudaFree(h->d_counter);
   cudaFree(h->d_sig);
   cudaFree(h->d_scales);
   cudaFree(h->d_out);
@@ -204,23 +213,24 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
   h->n_zero_runs = int(tab.zero_runs.size() / 2);
   h->win_len = tab.len;
 
-  // Sensor splits (cluster ranks) per tile: enough CTAs for two per SM.  The
-  // split is fixed per handle so the summation order never changes.
-  int split = 1;
-  while (split < 8 && int64_t(h->n_tiles) * split < 2 * int64_t(h->n_sm) &&
-         (n_sensors + 2 * split - 1) / (2 * split) >= 4)
-    split *= 2;
-  h->split = split;
-  h->split_len = round_up((n_sensors + split - 1) / split, 4);
+  // Segments of G sensors per tile: the unit of work balancing and of the
+  // fixed-order partial sums.  Fixed per handle so the summation order never
+  // changes with the launch shape or the batch.
+  h->G = 64;
+  h->n_seg = (n_sensors + h->G - 1) / h->G;
 
   std::vector<float> w(n_sensors);
   for (int s = 0; s < n_sensors; ++s) w[s] = weights_host ? weights_host[s] : 1.0f / float(n_sensors);
 
   // device form of base and window length: base in the low 16 bits, length
   // in the high 16 bits (n_samples <= 32768 keeps both in range)
-  std::vector<int32_t> packed(tab.base.size());
-  for (size_t i = 0; i < packed.size(); ++i)
-    packed[i] = int32_t(uint32_t(tab.base[i]) | (uint32_t(tab.len[i]) << 16));
+  // rows padded to N_s_pad entries so every segment's run is 16-byte aligned
+  std::vector<int32_t> packed(size_t(h->n_tiles) * h->ns_pad, 0);
+  for (int t = 0; t < h->n_tiles; ++t)
+    for (int s = 0; s < n_sensors; ++s) {
+      const size_t i = size_t(t) * n_sensors + s;
+      packed[size_t(t) * h->ns_pad + s] = int32_t(uint32_t(tab.base[i]) | (uint32_t(tab.len[i]) << 16));
+    }
   pat_status st;
   if ((st = upload(&h->d_u, tab.u, "table")) != PAT_OK ||
       (st = upload(&h->d_base, packed, "bases")) != PAT_OK ||
@@ -248,42 +258,54 @@ static int fmt_for(pat_dtype dt) {
   return dt == PAT_F32 ? kBF32 : (dt == PAT_BF16 ? kBBF16P : kBF16P);
 }
 
+static int frames_per_group(int n_frames) {
+  return n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1));
+}
+
+static pat_status grow_zeroed(void** p, size_t* cap, size_t need, const char* what) {
+  if (need <= *cap) return PAT_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) return fail(PAT_ERR_OOM, what);
+  PAT_CUDA(cudaMemset(*p, 0, need));
+  *cap = need;
+  return PAT_OK;
+}
+
 static pat_status ensure_buffers(pat_bp_t h, int n_frames) {
-  const size_t b_need = (size_t(n_frames) * h->ns * h->nt_pad + size_t(h->W) + 64) * 4;
-  if (b_need > h->b_cap) {
-    cudaFree(h->d_b);
-    h->d_b = nullptr;
-    h->b_cap = 0;
-    if (cudaMalloc(&h->d_b, b_need) != cudaSuccess) return fail(PAT_ERR_OOM, "integrand buffer");
-    PAT_CUDA(cudaMemset(h->d_b, 0, b_need));
-    h->b_cap = b_need;
-  }
-  const size_t m_need = size_t(n_frames) * h->ns_pad * sizeof(float);
-  if (m_need > h->m_cap) {
-    cudaFree(h->d_m);
-    h->d_m = nullptr;
-    h->m_cap = 0;
-    if (cudaMalloc(&h->d_m, m_need) != cudaSuccess) return fail(PAT_ERR_OOM, "multipliers");
-    PAT_CUDA(cudaMemset(h->d_m, 0, m_need));
-    h->m_cap = m_need;
+  const int FB = frames_per_group(n_frames);
+  const size_t n_fg = size_t((n_frames + FB - 1) / FB);
+  pat_status st;
+  const size_t b_need = (n_fg * h->ns * h->nt_pad + kTailRows) * FB * 4;
+  if ((st = grow_zeroed(&h->d_b, &h->b_cap, b_need, "integrand buffer")) != PAT_OK) return st;
+  const size_t m_need = n_fg * h->ns_pad * FB * sizeof(float);
+  if ((st = grow_zeroed(reinterpret_cast<void**>(&h->d_m), &h->m_cap, m_need, "multipliers")) != PAT_OK)
+    return st;
+  if (h->n_seg > 1) {
+    const size_t part_need = n_fg * h->n_tiles * h->n_seg * FB * h->P * sizeof(float);
+    if ((st = grow_zeroed(reinterpret_cast<void**>(&h->d_part), &h->part_cap, part_need,
+                          "segment partials")) != PAT_OK)
+      return st;
+    const size_t cnt_need = n_fg * h->n_tiles * sizeof(int);
+    if ((st = grow_zeroed(reinterpret_cast<void**>(&h->d_counter), &h->counter_cap, cnt_need,
+                          "segment counters")) != PAT_OK)
+      return st;
   }
   return PAT_OK;
 }
 
 // Largest sum of window lengths over the S-sensor stages of any tile: the
-// window entries one pipeline stage must hold per frame.
+// window rows one pipeline stage must hold.
 static int stage_window(pat_bp_t h, int S) {
   if (S >= 1 && S <= 32 && h->wst_cache[S]) return h->wst_cache[S];
   int best = 8;
   for (int t = 0; t < h->n_tiles; ++t) {
     const uint16_t* len = h->win_len.data() + size_t(t) * h->ns;
-    for (int r = 0; r < h->split; ++r) {
-      const int sb = r * h->split_len, se = std::min(h->ns, sb + h->split_len);
-      for (int s0 = sb; s0 < se; s0 += S) {
-        int sum = 0;
-        for (int s = s0; s < std::min(se, s0 + S); ++s) sum += len[s];
-        best = std::max(best, sum);
-      }
+    for (int s0 = 0; s0 < h->ns; s0 += S) {
+      int sum = 0;
+      for (int s = s0; s < std::min(h->ns, s0 + S); ++s) sum += len[s];
+      best = std::max(best, sum);
     }
   }
   best = round_up(best, 8);
@@ -291,20 +313,20 @@ static int stage_window(pat_bp_t h, int S) {
   return best;
 }
 
-// Launch shape for a frame count: frames per CTA, sensors per stage, stages.
+// Launch shape for a frame count: frames per unit, sensors per stage, stages.
 static GatherConfig pick_config(pat_bp_t h, int n_frames, int* wst) {
   GatherConfig c;
   c.P = h->P;
   c.SW = h->SW;
-  c.FB = n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1));
+  c.FB = frames_per_group(n_frames);
   c.S = c.FB == 1 ? 16 : 8;
-  const size_t budget = 110 * 1024;
+  const size_t budget = c.FB == 1 ? 72 * 1024 : 100 * 1024;
   c.stages = 6;
   for (;;) {
     *wst = stage_window(h, c.S);
-    while (c.stages > 2 && gather_smem_bytes(c, 0, *wst) > budget) --c.stages;
-    if (gather_smem_bytes(c, 0, *wst) <= budget || c.S <= c.SW) break;
-    c.S -= c.SW;
+    while (c.stages > 2 && gather_smem_bytes(c, *wst) > budget) --c.stages;
+    if (gather_smem_bytes(c, *wst) <= budget || c.S <= 8) break;
+    c.S -= 8;
   }
   return c;
 }
@@ -339,42 +361,59 @@ static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dty
   pp.n_t = h->nt;
   pp.n_t_pad = h->nt_pad;
   pp.n_frames = n_frames;
+  pp.FB = frames_per_group(n_frames);
   cudaError_t e = launch_preprocess(pp, stream);
   if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
   h->pre_frames = n_frames;
   h->pre_fmt = pp.fmt;
+  h->pre_fb = pp.FB;
   return PAT_OK;
 }
 
 static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaStream_t stream) {
   if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
-  if (n_frames < 1 || n_frames > h->pre_frames)
-    return fail(PAT_ERR_INVALID, "gather needs a preprocess of at least n_frames frames first");
+  if (n_frames < 1 || n_frames != h->pre_frames)
+    return fail(PAT_ERR_INVALID, "gather needs the preprocess of the same n_frames first");
   int wst = 0;
   GatherConfig c = pick_config(h, n_frames, &wst);
-  GatherParams gp;
-  gp.u = h->d_u;
-  gp.base = h->d_base;
-  gp.slot = h->d_slot;
-  gp.zero_runs = h->d_zero_runs;
-  gp.n_zero_runs = h->n_zero_runs;
-  gp.b = h->d_b;
-  gp.m = h->d_m;
-  gp.out = out_dev;
-  gp.out_stride = h->out_stride;
-  gp.n_sensors = h->ns;
-  gp.n_sensors_pad = h->ns_pad;
-  gp.n_t_pad = h->nt_pad;
-  gp.Wst = wst;
-  gp.n_tiles = h->n_tiles;
-  gp.n_frames = n_frames;
-  gp.S = c.S;
-  gp.stages = c.stages;
-  gp.split = h->split;
-  gp.split_len = h->split_len;
-  gp.status = h->d_status;
-  gp.timeout_ns = 2000000000ull;
-  cudaError_t e = launch_gather(c, h->pre_fmt, gp, stream);
+  if (c.FB != h->pre_fb) return fail(PAT_ERR_INVALID, "frame grouping changed since preprocess");
+  StreamParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  InstDesc& d = sp.inst[0];
+  d.u = h->d_u;
+  d.base = h->d_base;
+  d.slot = h->d_slot;
+  d.zero_runs = h->d_zero_runs;
+  d.n_zero_runs = h->n_zero_runs;
+  d.b = h->d_b;
+  d.m = h->d_m;
+  d.out = out_dev;
+  d.part = h->d_part;
+  d.counter = h->d_counter;
+  d.out_stride = h->out_stride;
+  d.unit_begin = 0;
+  d.n_sensors = h->ns;
+  d.n_sensors_pad = h->ns_pad;
+  d.n_t_pad = h->nt_pad;
+  d.n_tiles = h->n_tiles;
+  d.n_frames = n_frames;
+  d.n_fg = (n_frames + c.FB - 1) / c.FB;
+  d.n_seg = h->n_seg;
+  d.G = h->G;
+  d.Wst = wst;
+  sp.n_inst = 1;
+  sp.n_units = int64_t(d.n_fg) * d.n_tiles * d.n_seg;
+  sp.S = c.S;
+  sp.stages = c.stages;
+  sp.Wst = wst;
+  sp.status = h->d_status;
+  sp.timeout_ns = 2000000000ull;
+  const int fbi = c.FB == 1 ? 0 : (c.FB == 2 ? 1 : (c.FB == 4 ? 2 : 3));
+  int& res = h->resident[fbi][h->pre_fmt][c.S == 8 ? 1 : 0];
+  if (res == 0) res = gather_resident_ctas(c, h->pre_fmt, wst, h->n_sm);
+  if (res <= 0) return fail(PAT_ERR_CUDA, "gather kernel does not fit on the device");
+  const int grid = int(std::min<int64_t>(sp.n_units, res));
+  cudaError_t e = launch_gather(c, h->pre_fmt, sp, grid, stream);
   if (e != cudaSuccess) return cuda_fail(e, "gather launch");
   return PAT_OK;
 }
@@ -455,7 +494,9 @@ extern "C" pat_status pat_bp_reconstruct_host(pat_bp_t h, const void* signals_ho
   PAT_CUDA(cudaMemcpy(&flag, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     cudaMemset(h->d_status, 0, sizeof(int));
-    return fail(PAT_ERR_TIMEOUT, "a device wait ran out of time");
+    if (h->d_counter) cudaMemset(h->d_counter, 0, h->counter_cap);
+    return fail(flag & kStatusTimeout ? PAT_ERR_TIMEOUT : PAT_ERR_CUDA,
+                flag & kStatusTimeout ? "a device wait ran out of time" : "bad launch configuration");
   }
   return PAT_OK;
 }
@@ -468,7 +509,10 @@ extern "C" pat_status pat_bp_sync(pat_bp_t h, pat_stream_t stream) {
   PAT_CUDA(cudaMemcpy(&flag, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     PAT_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
-    return fail(PAT_ERR_TIMEOUT, "a device wait ran out of time");
+    // an aborted launch can leave segment counters part-way: start clean
+    if (h->d_counter) PAT_CUDA(cudaMemset(h->d_counter, 0, h->counter_cap));
+    return fail(flag & kStatusTimeout ? PAT_ERR_TIMEOUT : PAT_ERR_CUDA,
+                flag & kStatusTimeout ? "a device wait ran out of time" : "bad launch configuration");
   }
   return PAT_OK;
 }
@@ -483,7 +527,7 @@ extern "C" pat_status pat_bp_info(pat_bp_t h, pat_bp_info_t* info) {
   info->tile_pix = h->P;
   info->n_tiles = h->n_tiles;
   info->window = h->W;
-  info->split = h->split;
+  info->split = h->n_seg;
   info->sensor_warps = h->SW;
   info->table_bytes = int64_t(h->n_tiles) * h->ns * h->P * 4;
   info->build_seconds = h->build_seconds;
@@ -496,8 +540,11 @@ extern "C" pat_status pat_bp_table(pat_bp_t h, float* u_host, int32_t* base_host
   const size_t n = size_t(h->n_tiles) * h->ns;
   if (u_host) PAT_CUDA(cudaMemcpy(u_host, h->d_u, n * h->P * 4, cudaMemcpyDeviceToHost));
   if (base_host) {
-    PAT_CUDA(cudaMemcpy(base_host, h->d_base, n * 4, cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < n; ++i) base_host[i] &= 0xffff;
+    std::vector<int32_t> packed(size_t(h->n_tiles) * h->ns_pad);
+    PAT_CUDA(cudaMemcpy(packed.data(), h->d_base, packed.size() * 4, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < h->n_tiles; ++t)
+      for (int s = 0; s < h->ns; ++s)
+        base_host[size_t(t) * h->ns + s] = packed[size_t(t) * h->ns_pad + s] & 0xffff;
   }
   if (pix_host) PAT_CUDA(cudaMemcpy(pix_host, h->d_slot, size_t(h->n_tiles) * h->P * 4, cudaMemcpyDeviceToHost));
   return PAT_OK;
