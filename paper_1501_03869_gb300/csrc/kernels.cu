@@ -177,10 +177,15 @@ __device__ __forceinline__ void store_words(uint32_t* dst, const uint32_t (&w)[N
   }
 }
 
-// One CTA per (sensor, frame group): FB frame-interleaved integrand rows.
+// One CTA per (sensor, frame group) row; every thread owns K consecutive
+// samples of the row for all FB frames and issues all its loads before any
+// use.  Rows are written frame-interleaved, K * FB words per thread.
 template <int DT, int FMT, int FB>
 __global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
+  constexpr int K = 8;
   __shared__ float red[8][FB];
+  // let the gather that depends on this kernel start its prologue now
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int s = blockIdx.x, g = blockIdx.y;
   const int f0 = g * FB;
   const int fb_eff = min(FB, p.n_frames - f0);
@@ -194,6 +199,25 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
     row0[fb] = r * n;
     sc[fb] = p.scales ? p.scales[r] : 1.0f;
   }
+  // b_{k0..k0+K} of frame fb (K + 1 values; the last feeds the pair slope)
+  auto b_run = [&](int fb, int k0, float (&b)[K + 1]) {
+    float v[K + 3];  // p_{k0-1} .. p_{k0+K+1}
+#pragma unroll
+    for (int j = 0; j < K + 3; ++j) {
+      const int k = k0 - 1 + j;
+      v[j] = (k >= 0 && k < n) ? load_sample<DT>(p.sig, row0[fb] + k) * sc[fb] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const int k = k0 + j;
+      float r;
+      if (k >= n) r = 0.0f;
+      else if (k == 0) r = 2.0f * v[j + 1];
+      else if (k == n - 1) r = fmaf(-2.0f * float(k), v[j + 1] - v[j], 2.0f * v[j + 1]);
+      else r = fmaf(-float(k), v[j + 2] - v[j], 2.0f * v[j + 1]);
+      b[j] = r;
+    }
+  };
   float inv[FB], sigma[FB];
 #pragma unroll
   for (int fb = 0; fb < FB; ++fb) sigma[fb] = inv[fb] = 1.0f;
@@ -201,9 +225,15 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
     float mx[FB];
 #pragma unroll
     for (int fb = 0; fb < FB; ++fb) mx[fb] = 0.0f;
-    for (int k = threadIdx.x; k < n; k += blockDim.x)
+    for (int k0 = threadIdx.x * K; k0 < n; k0 += blockDim.x * K) {
 #pragma unroll
-      for (int fb = 0; fb < FB; ++fb) mx[fb] = fmaxf(mx[fb], fabsf(integrand<DT>(p.sig, row0[fb], sc[fb], k, n)));
+      for (int fb = 0; fb < FB; ++fb) {
+        float b[K + 1];
+        b_run(fb, k0, b);
+#pragma unroll
+        for (int j = 0; j < K; ++j) mx[fb] = fmaxf(mx[fb], fabsf(b[j]));
+      }
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
     for (int fb = 0; fb < FB; ++fb) {
@@ -221,23 +251,24 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
     }
   }
   uint32_t* dst = static_cast<uint32_t*>(p.b) + (int64_t(g) * p.n_sensors + s) * p.n_t_pad * FB;
-  for (int k = threadIdx.x; k < p.n_t_pad; k += blockDim.x) {
-    uint32_t wds[FB];
+  for (int k0 = threadIdx.x * K; k0 < p.n_t_pad; k0 += blockDim.x * K) {
+    uint32_t w[K * FB];
 #pragma unroll
     for (int fb = 0; fb < FB; ++fb) {
       if (fb < fb_eff) {
-        if constexpr (FMT == kBF32) {
-          wds[fb] = __float_as_uint(integrand<DT>(p.sig, row0[fb], sc[fb], k, n));
-        } else {
-          const float v0 = integrand<DT>(p.sig, row0[fb], sc[fb], k, n) * inv[fb];
-          const float v1 = integrand<DT>(p.sig, row0[fb], sc[fb], k + 1, n) * inv[fb];
-          wds[fb] = encode_pair<FMT>(v0, v1);
+        float b[K + 1];
+        b_run(fb, k0, b);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          if constexpr (FMT == kBF32) w[j * FB + fb] = __float_as_uint(b[j]);
+          else w[j * FB + fb] = encode_pair<FMT>(b[j] * inv[fb], b[j + 1] * inv[fb]);
         }
       } else {
-        wds[fb] = 0u;
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j * FB + fb] = 0u;
       }
     }
-    store_words<FB>(dst + int64_t(k) * FB, wds);
+    store_words<K * FB>(dst + int64_t(k0) * FB, w);
   }
   if (threadIdx.x < FB) {
     const int fb = threadIdx.x;
@@ -329,7 +360,7 @@ struct StageLayout {
   }
 };
 
-constexpr int kHeaderBytes = 256;   // mbarriers and flags
+constexpr int kHeaderBytes = 512;   // mbarriers, unit ring and flags
 constexpr int kMetaBytes = 2 * kMaxG * 4;
 
 struct UnitPos {
@@ -352,6 +383,13 @@ __device__ __forceinline__ UnitPos decode_unit(const StreamParams& p, int64_t u,
   return q;
 }
 
+constexpr int kRing = 16;  // unit indices in flight between the producer and the consumers
+
+// Warp roles: consumers 0..NWC-1 (gather), producer NWC (copies), epilogues
+// NWC+1 and NWC+2 (alternate units: phase sum, segment partials, tile sums).
+// Units are handed out by an atomic ticket (sched[0]); the last CTA to finish
+// resets the tickets (sched[1] counts finished CTAs), so a launch -- or a
+// replay of a captured graph -- always starts from zero.
 template <int P, int FB, int FMT, int SW>
 __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
     gather_kernel(const __grid_constant__ StreamParams p) {
@@ -361,16 +399,16 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + kMaxStages;
   uint64_t* meta_bar = empty + kMaxStages;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(meta_bar + 2);
+  int64_t* unit_ring = reinterpret_cast<int64_t*>(meta_bar + 2);  // [kRing]
+  int64_t* red_unit = unit_ring + kRing;                           // [2]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(red_unit + 2);
   int* meta = reinterpret_cast<int*>(smem + kHeaderBytes);  // [2][kMaxG] packed bases
   const StageLayout L(p.S, P, FB, p.Wst);
   unsigned char* stage0 = smem + kHeaderBytes + kMetaBytes;
   float* red = reinterpret_cast<float*>(stage0 + L.bytes * p.stages);  // [2][SW][FB][P]
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ua = int64_t(blockIdx.x) * p.n_units / gridDim.x;
-  const int64_t ub = int64_t(blockIdx.x + 1) * p.n_units / gridDim.x;
   const int S4 = (p.S + 3) & ~3;
+  const int64_t N = p.n_units;
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < p.stages; ++st) {
@@ -393,11 +431,15 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
   if (warp == NWC) {
     // ------------------------------------------------------------ producer --
     int inst = 0;
-    int64_t seq = 0;         // chunks issued by this CTA
-    int64_t meta_last = -1;  // last unit whose bases were requested
+    int64_t seq = 0;  // chunks (stage uses) issued by this CTA
+    auto abort_now = [&]() {
+      if (lane == 0) {
+        atomicOr(p.status, kStatusTimeout);
+        *abort_flag = 1;
+      }
+    };
     auto issue_meta = [&](int64_t u, int slot) {
-      meta_last = u;
-      int ii = inst;
+      int ii = 0;
       const UnitPos q = decode_unit(p, u, ii);
       const InstDesc& d = p.inst[q.inst];
       const uint32_t n4 = uint32_t((q.s_hi - q.s_lo + 3) & ~3);
@@ -408,31 +450,51 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
                  &meta_bar[slot]);
       }
     };
+    // wait until stage st may be refilled (its previous use consumed)
+    auto acquire_stage = [&](int st) -> bool {
+      const int64_t use = seq / p.stages;
+      if (use == 0) return true;
+      if (mbar_wait_bounded(&empty[st], uint32_t((use - 1) & 1), p.timeout_ns, abort_flag)) return true;
+      abort_now();
+      return false;
+    };
+    int64_t t_cur = 0, t_next = 0;
+    if (lane == 0) {
+      t_cur = atomicAdd(reinterpret_cast<unsigned long long*>(p.sched), 1ull);
+      t_next = t_cur < N ? int64_t(atomicAdd(reinterpret_cast<unsigned long long*>(p.sched), 1ull)) : N;
+    }
+    t_cur = __shfl_sync(0xffffffffu, t_cur, 0);
+    t_next = __shfl_sync(0xffffffffu, t_next, 0);
+    if (t_cur < N) issue_meta(t_cur, 0);
+    int64_t meta_last = t_cur < N ? 0 : -1;  // unit counter j of the last base copy requested
     bool ok = true;
-    if (ua < ub) issue_meta(ua, 0);
-    for (int64_t u = ua; u < ub && ok; ++u) {
-      const int64_t k = u - ua;
-      const int slot = int(k & 1);
-      const UnitPos q = decode_unit(p, u, inst);
+    bool waited_inputs = false;
+    int64_t j = 0;
+    for (; t_cur < N && ok; ++j) {
+      const int slot = int(j & 1);
+      const UnitPos q = decode_unit(p, t_cur, inst);
       const InstDesc& d = p.inst[q.inst];
-      if (!mbar_wait_bounded(&meta_bar[slot], uint32_t((k >> 1) & 1), p.timeout_ns, abort_flag)) {
-        if (lane == 0) {
-          atomicOr(p.status, kStatusTimeout);
-          *abort_flag = 1;
-        }
+      if (!mbar_wait_bounded(&meta_bar[slot], uint32_t((j >> 1) & 1), p.timeout_ns, abort_flag)) {
+        abort_now();
         break;
       }
       __syncwarp();
-      if (u + 1 < ub) issue_meta(u + 1, slot ^ 1);
+      int64_t t_next2 = N;
+      if (t_next < N) {
+        issue_meta(t_next, slot ^ 1);
+        meta_last = j + 1;
+        if (lane == 0) t_next2 = int64_t(atomicAdd(reinterpret_cast<unsigned long long*>(p.sched), 1ull));
+      }
+      if (lane == 0) unit_ring[j % kRing] = t_cur;
+      if (!waited_inputs) {
+        // the integrand and multipliers come from the preprocessing grid
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        waited_inputs = true;
+      }
       const int* mrow = meta + slot * kMaxG;
       for (int s0 = q.s_lo; s0 < q.s_hi; s0 += p.S, ++seq) {
         const int st = int(seq % p.stages);
-        const int64_t use = seq / p.stages;
-        if (use > 0 && !mbar_wait_bounded(&empty[st], uint32_t((use - 1) & 1), p.timeout_ns, abort_flag)) {
-          if (lane == 0) {
-            atomicOr(p.status, kStatusTimeout);
-            *abort_flag = 1;
-          }
+        if (!acquire_stage(st)) {
           ok = false;
           break;
         }
@@ -463,9 +525,8 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
         if (lane < S4) reinterpret_cast<int*>(sb + L.off)[lane] = lane < se ? off : 0;
         __syncwarp();
         const uint32_t bytes = uint32_t(se) * P * 4 + uint32_t(se4) * FB * 4 + wrows * FB * 4;
-        if (lane == 0) mbar_arrive_expect_tx(&full[st], bytes);
-        __syncwarp();
         if (lane == 0) {
+          mbar_arrive_expect_tx(&full[st], bytes);
           bulk_g2s(sb + L.u, d.u + (int64_t(q.tile) * d.n_sensors + s0) * P, uint32_t(se) * P * 4,
                    &full[st]);
           bulk_g2s(sb + L.m, d.m + (int64_t(q.fg) * d.n_sensors_pad + s0) * FB,
@@ -478,39 +539,54 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
           bulk_g2s(sb + L.win + size_t(off) * FB * 4, src, uint32_t(wl) * FB * 4, &full[st]);
         }
       }
+      t_cur = t_next;
+      t_next = __shfl_sync(0xffffffffu, t_next2, 0);
+    }
+    // end of work: an empty stage whose unit index is -1
+    if (ok) {
+      const int st = int(seq % p.stages);
+      if (acquire_stage(st)) {
+        if (lane == 0) {
+          unit_ring[j % kRing] = -1;
+          mbar_arrive(&full[st]);
+        }
+        ++seq;
+      }
     }
     // drain the copies still in flight before the CTA may exit
     for (int64_t c = seq > p.stages ? seq - p.stages : 0; c < seq; ++c)
       mbar_wait_bounded(&full[c % p.stages], uint32_t((c / p.stages) & 1), p.timeout_ns, nullptr);
-    if (meta_last >= 0) {
-      // the last base copy (one unit ahead) may still be in flight after an abort
-      const int64_t k = meta_last - ua;
-      mbar_wait_bounded(&meta_bar[k & 1], uint32_t((k >> 1) & 1), p.timeout_ns, nullptr);
-    }
+    if (meta_last >= 0)
+      mbar_wait_bounded(&meta_bar[meta_last & 1], uint32_t((meta_last >> 1) & 1), p.timeout_ns, nullptr);
   } else if (warp < NWC) {
     // ------------------------------------------------------------ consumers --
     const int pg = warp % PW, sp = warp / PW;
     int inst = 0;
-    int64_t seq = 0;
+    int64_t seq = 0, j = 0;
     bool ok = true;
-    for (int64_t u = ua; u < ub; ++u) {
+    auto wait_full = [&](int st) -> bool {
+      if (mbar_wait_bounded(&full[st], uint32_t((seq / p.stages) & 1), p.timeout_ns, abort_flag)) return true;
+      if (lane == 0) {
+        atomicOr(p.status, kStatusTimeout);
+        *abort_flag = 1;
+      }
+      return false;
+    };
+    for (;; ++j) {
+      if (!wait_full(int(seq % p.stages))) break;
+      const int64_t u = unit_ring[j % kRing];
+      if (u < 0) break;
       const UnitPos q = decode_unit(p, u, inst);
-      const int64_t j = u - ua;
       float acc[FB][4];
 #pragma unroll
       for (int fb = 0; fb < FB; ++fb)
 #pragma unroll
         for (int x = 0; x < 4; ++x) acc[fb][x] = 0.0f;
       for (int s0 = q.s_lo; s0 < q.s_hi; s0 += p.S, ++seq) {
-        if (!ok) continue;  // after an abort: keep the epilogue hand-off going, compute nothing
         const int st = int(seq % p.stages);
-        if (!mbar_wait_bounded(&full[st], uint32_t((seq / p.stages) & 1), p.timeout_ns, abort_flag)) {
-          if (lane == 0) {
-            atomicOr(p.status, kStatusTimeout);
-            *abort_flag = 1;
-          }
+        if (s0 != q.s_lo && !wait_full(st)) {
           ok = false;
-          continue;
+          break;
         }
         const int se = min(p.S, q.s_hi - s0);
         const unsigned char* sb = stage0 + st * L.bytes;
@@ -527,7 +603,8 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
       }
-      // hand the unit's sums to the epilogue warp through red[j & 1]
+      if (!ok) break;
+      // hand the unit's sums to the epilogue warp j & 1 through red[j & 1]
       const int buf = int(j & 1);
       if (j >= 2) red_free_sync(buf, (NWC + 1) * 32);
       float* rb = red + size_t(buf) * SW * FB * P;
@@ -535,11 +612,19 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
       for (int fb = 0; fb < FB; ++fb)
 #pragma unroll
         for (int x = 0; x < 4; ++x) rb[(sp * FB + fb) * P + pg * 128 + x * 32 + lane] = acc[fb][x];
+      if (threadIdx.x == 0) red_unit[buf] = u;
+      red_full_arrive(buf, (NWC + 1) * 32);
+    }
+    // no more units: one end marker for each epilogue warp
+    for (int e = 0; e < 2; ++e) {
+      const int64_t idx = j + e;
+      const int buf = int(idx & 1);
+      if (idx >= 2) red_free_sync(buf, (NWC + 1) * 32);
+      if (threadIdx.x == 0) red_unit[buf] = -1;
       red_full_arrive(buf, (NWC + 1) * 32);
     }
   } else {
     // ------------------------------------------------------------ epilogues --
-    // Two epilogue warps take alternate units (ew = unit parity = red buffer).
     const int ew = warp - NWC - 1;
     for (int i = 0; i < p.n_inst; ++i) {
       const InstDesc& d = p.inst[i];
@@ -552,18 +637,15 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
     }
     constexpr int KO = P / 32;  // outputs of one frame per lane
     int inst = 0;
-    for (int64_t u = ua + ew; u < ub; u += 2) {
+    for (;;) {
+      red_full_sync(ew, (NWC + 1) * 32);
+      const int64_t u = red_unit[ew];
+      if (u < 0) break;
       const UnitPos q = decode_unit(p, u, inst);
       const InstDesc& d = p.inst[q.inst];
-      const int buf = ew;
       const int f0 = q.fg * FB;
       const int fb_eff = min(FB, d.n_frames - f0);
-      int slot_idx[KO];
-#pragma unroll
-      for (int k = 0; k < KO; ++k) slot_idx[k] = __ldg(d.slot + int64_t(q.tile) * P + k * 32 + lane);
-      red_full_sync(buf, (NWC + 1) * 32);
-      const float* rb = red + size_t(buf) * SW * FB * P;
-      const int64_t pbase = ((int64_t(q.fg) * d.n_tiles + q.tile) * d.n_seg) * FB * P;
+      const float* rb = red + size_t(ew) * SW * FB * P;
       float v[FB][KO];
 #pragma unroll
       for (int fb = 0; fb < FB; ++fb)
@@ -575,7 +657,11 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
           for (int ph = 0; ph < SW; ++ph) a += rb[ph * FB * P + o];  // fixed phase order
           v[fb][k] = a;
         }
-      if (u + 2 < ub) red_free_arrive(buf, (NWC + 1) * 32);  // red[buf] free again
+      red_free_arrive(ew, (NWC + 1) * 32);  // red[ew] free again
+      int slot_idx[KO];
+#pragma unroll
+      for (int k = 0; k < KO; ++k) slot_idx[k] = __ldg(d.slot + int64_t(q.tile) * P + k * 32 + lane);
+      const int64_t pbase = ((int64_t(q.fg) * d.n_tiles + q.tile) * d.n_seg) * FB * P;
       if (d.n_seg == 1) {
 #pragma unroll
         for (int fb = 0; fb < FB; ++fb)
@@ -617,6 +703,15 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
       }
       __syncwarp();
       if (lane == 0) atomicExch(d.counter + int64_t(q.fg) * d.n_tiles + q.tile, 0);
+    }
+  }
+  // the last CTA out resets the unit tickets for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(p.sched + 2, 1u) == gridDim.x - 1) {
+      atomicExch(reinterpret_cast<unsigned long long*>(p.sched), 0ull);
+      atomicExch(p.sched + 2, 0u);
     }
   }
 }
@@ -683,8 +778,17 @@ static cudaError_t gather_t(const StreamParams& p, size_t smem, int grid, cudaSt
     *resident = per_sm * n_sm;
     return cudaSuccess;
   }
-  kern<<<grid, threads, smem, st>>>(p);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 template <int P, int FMT, int SW>

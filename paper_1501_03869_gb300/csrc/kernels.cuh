@@ -62,6 +62,7 @@ struct StreamParams {
   int stages;               // pipeline depth
   int Wst;                  // window rows one stage can need (max over instances)
   int* status;
+  unsigned* sched;          // [4] zero-initialised: unit ticket (64-bit) and CTAs finished
   uint64_t timeout_ns;
 };
 

@@ -72,6 +72,7 @@ struct pat_bp_s {
   int32_t* d_zero_runs = nullptr;
   float* d_w = nullptr;
   int* d_status = nullptr;
+  unsigned* d_sched = nullptr;        // gather unit tickets (self-resetting)
   void* d_b = nullptr;
   size_t b_cap = 0;
   float* d_m = nullptr;
@@ -141,6 +142,7 @@ static void free_handle(pat_bp_t h) {
   cudaFree(h->d_zero_runs);
   cudaFree(h->d_w);
   cudaFree(h->d_status);
+  cudaFree(h->d_sched);
   cudaFree(h->d_b);
   cudaFree(h->d_m);
   cudaFree(h->d_part);
@@ -245,6 +247,11 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
     return fail(PAT_ERR_OOM, "status word");
   }
   cudaMemset(h->d_status, 0, sizeof(int));
+  if (cudaMalloc(&h->d_sched, 4 * sizeof(unsigned)) != cudaSuccess) {
+    free_handle(h);
+    return fail(PAT_ERR_OOM, "scheduler words");
+  }
+  cudaMemset(h->d_sched, 0, 4 * sizeof(unsigned));
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_handle(h);
@@ -320,7 +327,7 @@ static GatherConfig pick_config(pat_bp_t h, int n_frames, int* wst) {
   c.SW = h->SW;
   c.FB = frames_per_group(n_frames);
   c.S = c.FB == 1 ? 16 : 8;
-  const size_t budget = c.FB == 1 ? 72 * 1024 : 100 * 1024;
+  const size_t budget = c.FB == 1 ? 55 * 1024 : 100 * 1024;
   c.stages = 6;
   for (;;) {
     *wst = stage_window(h, c.S);
@@ -407,6 +414,7 @@ static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaSt
   sp.stages = c.stages;
   sp.Wst = wst;
   sp.status = h->d_status;
+  sp.sched = h->d_sched;
   sp.timeout_ns = 2000000000ull;
   const int fbi = c.FB == 1 ? 0 : (c.FB == 2 ? 1 : (c.FB == 4 ? 2 : 3));
   int& res = h->resident[fbi][h->pre_fmt][c.S == 8 ? 1 : 0];
@@ -495,6 +503,7 @@ extern "C" pat_status pat_bp_reconstruct_host(pat_bp_t h, const void* signals_ho
   if (flag) {
     cudaMemset(h->d_status, 0, sizeof(int));
     if (h->d_counter) cudaMemset(h->d_counter, 0, h->counter_cap);
+    cudaMemset(h->d_sched, 0, 4 * sizeof(unsigned));
     return fail(flag & kStatusTimeout ? PAT_ERR_TIMEOUT : PAT_ERR_CUDA,
                 flag & kStatusTimeout ? "a device wait ran out of time" : "bad launch configuration");
   }
@@ -509,8 +518,9 @@ extern "C" pat_status pat_bp_sync(pat_bp_t h, pat_stream_t stream) {
   PAT_CUDA(cudaMemcpy(&flag, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     PAT_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
-    // an aborted launch can leave segment counters part-way: start clean
+    // an aborted launch can leave counters part-way: start clean
     if (h->d_counter) PAT_CUDA(cudaMemset(h->d_counter, 0, h->counter_cap));
+    PAT_CUDA(cudaMemset(h->d_sched, 0, 4 * sizeof(unsigned)));
     return fail(flag & kStatusTimeout ? PAT_ERR_TIMEOUT : PAT_ERR_CUDA,
                 flag & kStatusTimeout ? "a device wait ran out of time" : "bad launch configuration");
   }
