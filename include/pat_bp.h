@@ -171,6 +171,73 @@ pat_status pat_table_host(const float* speed_host, const pat_grid* grid, const d
                           unsigned flags, pat_bp_info_t* info, float* u_host, int32_t* base_host,
                           int32_t* slot_host);
 
+/* ------------------------------------------------------------------------
+ * Many instances in one persistent launch (uneven grids, sensor counts,
+ * sample counts and frame counts).  A plan fixes the handles and their frame
+ * counts; each execution streams the preprocessing of every instance in one
+ * launch and the back projection of every instance in one persistent gather
+ * launch (programmatically dependent on the first), optionally as a CUDA
+ * graph.  The summation order of every instance is its handle's own, so each
+ * image is bit-identical to that handle's pat_bp_reconstruct of the same
+ * frames, whatever else is in the plan or however the launch is shaped.
+ * ------------------------------------------------------------------------ */
+typedef struct pat_plan_s* pat_plan_t;
+
+#define PAT_PLAN_AUTOTUNE 0x1u /* time candidate launch shapes at the first execution */
+#define PAT_PLAN_GRAPH 0x2u    /* capture the two launches once, replay a CUDA graph */
+
+typedef struct {
+  int n_inst;
+  int frames_per_unit;   /* FB: frames that share one pass over a table tile  */
+  int sensors_per_stage; /* S                                                  */
+  int stages;            /* pipeline depth of the gather                       */
+  int smem_budget_kb;    /* shared memory per CTA the shape was sized for      */
+  int grid;              /* persistent CTAs of the gather launch               */
+  int64_t n_units;       /* work units (frame group, tile, sensor segment)     */
+  int tuned;             /* 1 once the autotuner chose the shape               */
+  int graph;             /* 1 once a CUDA graph is captured                    */
+  double tune_ms;        /* best measured time per execution while tuning      */
+} pat_plan_info_t;
+
+/* pat_plan_create -- n (1..64) distinct handles of one device, all with the
+ * same tile size, each with n_frames[i] frames per execution, all signals of
+ * dtype.  Allocates the per-handle integrand and scratch buffers.  Errors:
+ * PAT_ERR_INVALID (duplicates, mixed tile sizes, bad counts), PAT_ERR_OOM. */
+pat_status pat_plan_create(const pat_bp_t* handles, const int* n_frames, int n, pat_dtype dtype,
+                           unsigned flags, pat_plan_t* out);
+
+/* pat_plan_execute -- signals_dev[i] [n_frames[i]][N_s][N_t], scales_dev[i]
+ * (required for 16-bit dtypes, else may be NULL or hold NULLs), outs_dev[i] as
+ * in pat_bp_reconstruct.  Asynchronous on stream, except that the first call
+ * of an autotuning plan synchronises while it times candidate shapes (that
+ * call must not be captured by the caller).  Executions of one plan, and of
+ * plans or calls sharing a handle, must not overlap on the GPU. */
+pat_status pat_plan_execute(pat_plan_t plan, const void* const* signals_dev,
+                            const float* const* scales_dev, float* const* outs_dev,
+                            pat_stream_t stream);
+
+/* pat_plan_sync -- wait for stream and report a device-side timeout of the
+ * plan's launches (PAT_ERR_TIMEOUT), clearing it. */
+pat_status pat_plan_sync(pat_plan_t plan, pat_stream_t stream);
+
+pat_status pat_plan_info(pat_plan_t plan, pat_plan_info_t* info);
+pat_status pat_plan_destroy(pat_plan_t plan);
+
+/* pat_bp_reconstruct_multi -- one-shot plan (no tuning, no graph) executed on
+ * stream; same arguments as pat_plan_create + pat_plan_execute. */
+pat_status pat_bp_reconstruct_multi(const pat_bp_t* handles, const void* const* signals_dev,
+                                    pat_dtype dtype, const float* const* scales_dev,
+                                    const int* n_frames, float* const* outs_dev, int n,
+                                    pat_stream_t stream);
+
+/* pat_bp_autotune -- time candidate launch shapes for n_frames frames of dtype
+ * on these inputs (the output is written with the correct result) and keep the
+ * fastest for later pat_bp_reconstruct / pat_bp_gather calls of the handle
+ * with the same frames-per-unit grouping.  Synchronous. */
+pat_status pat_bp_autotune(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                           const float* scales_dev, int n_frames, float* out_dev,
+                           pat_stream_t stream);
+
 /* pat_test_wait_timeout -- launches one CTA whose mbarrier wait can never
  * complete, bounded by timeout_ns; returns PAT_ERR_TIMEOUT when the kernel
  * gave up and reported it, PAT_OK if it (wrongly) completed.  Exercises the

@@ -20,7 +20,8 @@ import numpy as np
 from . import _lib
 from ._lib import PatError
 
-__all__ = ["BP", "PatError", "fmm_host", "table_host", "wait_timeout_probe", "DTYPES"]
+__all__ = ["BP", "Plan", "PatError", "fmm_host", "table_host", "reconstruct_multi",
+           "wait_timeout_probe", "DTYPES"]
 
 DTYPES = {"f32": _lib.PAT_F32, "bf16": _lib.PAT_BF16, "f16": _lib.PAT_F16}
 
@@ -186,6 +187,20 @@ class BP:
             out.ctypes.data), "pat_bp_reconstruct_host")
         return out
 
+    def autotune(self, signals, scales=None, out=None, stream=None):
+        """Time launch shapes for this frame count on these inputs; later calls
+        with the same frames-per-unit grouping use the fastest."""
+        if signals.dim() == 2:
+            signals = signals.unsqueeze(0)
+        F = signals.shape[0]
+        if out is None:
+            out = _torch().empty(self.out_shape(F), dtype=_torch().float32, device=signals.device)
+        _lib.check(self._lib.pat_bp_autotune(
+            self._h, ctypes.c_void_p(signals.data_ptr()), _dtype_code(signals),
+            None if scales is None else ctypes.c_void_p(scales.data_ptr()), F,
+            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "pat_bp_autotune")
+        return out
+
     def reserve(self, max_frames, dtype="f32"):
         _lib.check(self._lib.pat_bp_reserve(self._h, int(max_frames), DTYPES[dtype]),
                    "pat_bp_reserve")
@@ -202,6 +217,88 @@ class BP:
         _lib.check(self._lib.pat_bp_table(self._h, u.ctypes.data, b.ctypes.data, s.ctypes.data),
                    "pat_bp_table")
         return u, b, s
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+def _tensor_ptrs(ts):
+    return _ptr_array([None if t is None else t.data_ptr() for t in ts])
+
+
+class Plan:
+    """Several handles reconstructed by one persistent launch (uneven grids,
+    sensor, sample and frame counts); optionally autotuned and replayed as a
+    CUDA graph.  frames[i] frames of handle bps[i] per execution."""
+
+    def __init__(self, bps, frames, dtype="f32", autotune=False, graph=False):
+        lib = _lib.load()
+        self._lib = lib
+        self.bps = list(bps)
+        self.frames = [int(f) for f in frames]
+        if len(self.frames) != len(self.bps):
+            raise ValueError("one frame count per handle")
+        self.dtype = dtype
+        flags = (_lib.PAT_PLAN_AUTOTUNE if autotune else 0) | (_lib.PAT_PLAN_GRAPH if graph else 0)
+        hs = _ptr_array([b.handle.value for b in self.bps])
+        fr = (ctypes.c_int * len(self.frames))(*self.frames)
+        h = ctypes.c_void_p()
+        _lib.check(lib.pat_plan_create(hs, fr, len(self.bps), DTYPES[dtype], flags, ctypes.byref(h)),
+                   "pat_plan_create")
+        self._h = h
+
+    def out_shapes(self):
+        return [b.out_shape(f) for b, f in zip(self.bps, self.frames)]
+
+    def execute(self, signals, outs, scales=None, stream=None):
+        if len(signals) != len(self.bps) or len(outs) != len(self.bps):
+            raise ValueError("one signal tensor and one output per handle")
+        for b, f, s, o in zip(self.bps, self.frames, signals, outs):
+            if not s.is_cuda or not s.is_contiguous() or tuple(s.shape) != (f, b.n_sensors, b.n_samples):
+                raise ValueError("signals must be contiguous CUDA tensors [F, ns, nt]")
+            if not o.is_contiguous() or o.numel() != int(np.prod(b.out_shape(f))):
+                raise ValueError("outs must be contiguous float32 tensors of the output shapes")
+        sc = None if scales is None else _tensor_ptrs(scales)
+        _lib.check(self._lib.pat_plan_execute(self._h, _tensor_ptrs(signals), sc, _tensor_ptrs(outs),
+                                              _stream_ptr(stream)), "pat_plan_execute")
+        return outs
+
+    def sync(self, stream=None):
+        _lib.check(self._lib.pat_plan_sync(self._h, _stream_ptr(stream)), "pat_plan_sync")
+
+    @property
+    def info(self):
+        inf = _lib.PatPlanInfo()
+        _lib.check(self._lib.pat_plan_info(self._h, ctypes.byref(inf)), "pat_plan_info")
+        return {k: getattr(inf, k) for k, _ in _lib.PatPlanInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pat_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reconstruct_multi(bps, signals, outs, scales=None, stream=None):
+    """One-shot multi-instance launch (no tuning, no graph)."""
+    lib = _lib.load()
+    code = _dtype_code(signals[0])
+    hs = _ptr_array([b.handle.value for b in bps])
+    fr = (ctypes.c_int * len(bps))(*[int(s.shape[0]) for s in signals])
+    sc = None if scales is None else _tensor_ptrs(scales)
+    _lib.check(lib.pat_bp_reconstruct_multi(hs, _tensor_ptrs(signals), code, sc, fr,
+                                            _tensor_ptrs(outs), len(bps), _stream_ptr(stream)),
+               "pat_bp_reconstruct_multi")
+    return outs
 
 
 def fmm_host(speed, dx, origin, src):

@@ -26,8 +26,11 @@ EXPORTS = (
     "pat_bp_preprocess", "pat_bp_gather",
     "pat_bp_reconstruct_host", "pat_bp_reserve", "pat_bp_sync", "pat_bp_info",
     "pat_bp_table", "pat_bp_destroy", "pat_fmm_host", "pat_table_host",
-    "pat_test_wait_timeout",
+    "pat_test_wait_timeout", "pat_plan_create", "pat_plan_execute", "pat_plan_sync",
+    "pat_plan_info", "pat_plan_destroy", "pat_bp_reconstruct_multi", "pat_bp_autotune",
 )
+PAT_PLAN_AUTOTUNE = 0x1
+PAT_PLAN_GRAPH = 0x2
 
 
 class PatGrid(ctypes.Structure):
@@ -42,6 +45,14 @@ class PatInfo(ctypes.Structure):
                 ("n_tiles", ctypes.c_int), ("window", ctypes.c_int), ("split", ctypes.c_int),
                 ("sensor_warps", ctypes.c_int), ("table_bytes", ctypes.c_int64),
                 ("build_seconds", ctypes.c_double)]
+
+
+class PatPlanInfo(ctypes.Structure):
+    _fields_ = [("n_inst", ctypes.c_int), ("frames_per_unit", ctypes.c_int),
+                ("sensors_per_stage", ctypes.c_int), ("stages", ctypes.c_int),
+                ("smem_budget_kb", ctypes.c_int), ("grid", ctypes.c_int),
+                ("n_units", ctypes.c_int64), ("tuned", ctypes.c_int), ("graph", ctypes.c_int),
+                ("tune_ms", ctypes.c_double)]
 
 
 class PatError(RuntimeError):
@@ -100,6 +111,21 @@ def load():
         lib.pat_table_host.restype = _i
         lib.pat_table_host.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp, _d, _i, _u,
                                        ctypes.POINTER(PatInfo), _vp, _vp, _vp]
+        _pp = ctypes.POINTER(_vp)
+        lib.pat_plan_create.restype = _i
+        lib.pat_plan_create.argtypes = [_pp, ctypes.POINTER(_i), _i, _i, _u, _pp]
+        lib.pat_plan_execute.restype = _i
+        lib.pat_plan_execute.argtypes = [_vp, _pp, _pp, _pp, _vp]
+        lib.pat_plan_sync.restype = _i
+        lib.pat_plan_sync.argtypes = [_vp, _vp]
+        lib.pat_plan_info.restype = _i
+        lib.pat_plan_info.argtypes = [_vp, ctypes.POINTER(PatPlanInfo)]
+        lib.pat_plan_destroy.restype = _i
+        lib.pat_plan_destroy.argtypes = [_vp]
+        lib.pat_bp_reconstruct_multi.restype = _i
+        lib.pat_bp_reconstruct_multi.argtypes = [_pp, _pp, _i, _pp, ctypes.POINTER(_i), _pp, _i, _vp]
+        lib.pat_bp_autotune.restype = _i
+        lib.pat_bp_autotune.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp]
         lib.pat_test_wait_timeout.restype = _i
         lib.pat_test_wait_timeout.argtypes = [_u64]
         _lib = lib

@@ -181,12 +181,9 @@ __device__ __forceinline__ void store_words(uint32_t* dst, const uint32_t (&w)[N
 // samples of the row for all FB frames and issues all its loads before any
 // use.  Rows are written frame-interleaved, K * FB words per thread.
 template <int DT, int FMT, int FB>
-__global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
+__device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g) {
   constexpr int K = 8;
   __shared__ float red[8][FB];
-  // let the gather that depends on this kernel start its prologue now
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int s = blockIdx.x, g = blockIdx.y;
   const int f0 = g * FB;
   const int fb_eff = min(FB, p.n_frames - f0);
   const int n = p.n_t;
@@ -278,6 +275,30 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
       if (q == fb && fb < fb_eff) mval = p.weights[s] * sigma[q];
     p.m[(int64_t(g) * p.n_sensors_pad + s) * FB + fb] = mval;
   }
+}
+
+template <int DT, int FMT, int FB>
+__global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
+  // let the gather that depends on this kernel start its prologue now
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  preprocess_row<DT, FMT, FB>(p, blockIdx.x, blockIdx.y);
+}
+
+// Several instances in one launch: CTA x belongs to the instance whose range
+// [cta_begin[i], cta_begin[i+1]) holds it; inside it, (sensor, frame group).
+template <int DT, int FMT, int FB>
+__global__ void __launch_bounds__(256) preprocess_multi_kernel(const __grid_constant__ PreMultiParams p) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  int lo = 0, hi = p.n_inst - 1;
+  const int64_t x = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.cta_begin[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  const PreParams& q = p.inst[lo];
+  const int64_t loc = x - p.cta_begin[lo];
+  preprocess_row<DT, FMT, FB>(q, int(loc % q.n_sensors), int(loc / q.n_sensors));
 }
 
 // ------------------------------------------------------------------ gather --
@@ -753,6 +774,35 @@ static cudaError_t launch_pre_fb(const PreParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int DT, int FMT>
+static cudaError_t launch_pre_multi_fb(const PreMultiParams& p, cudaStream_t st) {
+  const int64_t ctas = p.cta_begin[p.n_inst];
+  if (ctas <= 0) return cudaSuccess;
+  const dim3 grid(static_cast<unsigned>(ctas), 1u, 1u);
+  switch (p.FB) {
+    case 1: preprocess_multi_kernel<DT, FMT, 1><<<grid, 256, 0, st>>>(p); break;
+    case 2: preprocess_multi_kernel<DT, FMT, 2><<<grid, 256, 0, st>>>(p); break;
+    case 4: preprocess_multi_kernel<DT, FMT, 4><<<grid, 256, 0, st>>>(p); break;
+    case 8: preprocess_multi_kernel<DT, FMT, 8><<<grid, 256, 0, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_multi(const PreMultiParams& p, cudaStream_t st) {
+  if (p.n_inst < 1 || p.n_inst > kMaxInst) return cudaErrorInvalidValue;
+  for (int i = 0; i < p.n_inst; ++i)
+    if (p.inst[i].dtype != p.dtype || p.inst[i].fmt != p.fmt || p.inst[i].FB != p.FB)
+      return cudaErrorInvalidValue;
+  if (p.dtype == 0 && p.fmt == kBF32) return launch_pre_multi_fb<0, kBF32>(p, st);
+  if (p.dtype == 1 && p.fmt == kBBF16P) return launch_pre_multi_fb<1, kBBF16P>(p, st);
+  if (p.dtype == 2 && p.fmt == kBF16P) return launch_pre_multi_fb<2, kBF16P>(p, st);
+  return cudaErrorInvalidValue;
+}
+
+const void* gather_kernel_func(const GatherConfig& c, int fmt);
+const void* preprocess_multi_func(int dtype, int fmt, int FB);
+
 cudaError_t launch_preprocess(const PreParams& p, cudaStream_t st) {
   if (p.dtype == 0 && p.fmt == kBF32) return launch_pre_fb<0, kBF32>(p, st);
   if (p.dtype == 1 && p.fmt == kBBF16P) return launch_pre_fb<1, kBBF16P>(p, st);
@@ -835,6 +885,49 @@ cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p,
     if (p.inst[i].G % p.S || p.inst[i].G > kMaxG || p.inst[i].Wst > p.Wst) return cudaErrorInvalidValue;
   if (p.n_units == 0) return cudaSuccess;
   return gather_dispatch(c, fmt, p, grid, st, nullptr, 0);
+}
+
+// Kernel entry addresses (identify graph nodes when refreshing their parameters).
+template <int P, int FMT, int SW>
+static const void* gather_func_fb(int FB) {
+  switch (FB) {
+    case 1: return reinterpret_cast<const void*>(gather_kernel<P, 1, FMT, SW>);
+    case 2: return reinterpret_cast<const void*>(gather_kernel<P, 2, FMT, SW>);
+    case 4: return reinterpret_cast<const void*>(gather_kernel<P, 4, FMT, SW>);
+    case 8: return reinterpret_cast<const void*>(gather_kernel<P, 8, FMT, SW>);
+  }
+  return nullptr;
+}
+
+const void* gather_kernel_func(const GatherConfig& c, int fmt) {
+  if (c.P == 128 && c.SW == 4) {
+    if (fmt == kBF32) return gather_func_fb<128, kBF32, 4>(c.FB);
+    if (fmt == kBBF16P) return gather_func_fb<128, kBBF16P, 4>(c.FB);
+    if (fmt == kBF16P) return gather_func_fb<128, kBF16P, 4>(c.FB);
+  } else if (c.P == 256 && c.SW == 2) {
+    if (fmt == kBF32) return gather_func_fb<256, kBF32, 2>(c.FB);
+    if (fmt == kBBF16P) return gather_func_fb<256, kBBF16P, 2>(c.FB);
+    if (fmt == kBF16P) return gather_func_fb<256, kBF16P, 2>(c.FB);
+  }
+  return nullptr;
+}
+
+template <int DT, int FMT>
+static const void* pre_multi_func_fb(int FB) {
+  switch (FB) {
+    case 1: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 1>);
+    case 2: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 2>);
+    case 4: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 4>);
+    case 8: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 8>);
+  }
+  return nullptr;
+}
+
+const void* preprocess_multi_func(int dtype, int fmt, int FB) {
+  if (dtype == 0 && fmt == kBF32) return pre_multi_func_fb<0, kBF32>(FB);
+  if (dtype == 1 && fmt == kBBF16P) return pre_multi_func_fb<1, kBBF16P>(FB);
+  if (dtype == 2 && fmt == kBF16P) return pre_multi_func_fb<2, kBF16P>(FB);
+  return nullptr;
 }
 
 cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t st) {

@@ -35,6 +35,13 @@ struct PreParams {
   int n_sensors, n_sensors_pad, n_t, n_t_pad, n_frames;
 };
 
+// Preprocessing of several instances in one launch (same dtype, format, FB).
+struct PreMultiParams {
+  PreParams inst[kMaxInst];
+  int64_t cta_begin[kMaxInst + 1];  // prefix sums of N_s * n_fg per instance
+  int n_inst, dtype, fmt, FB;
+};
+
 // One speed map's on-line data for a gather launch.  Work is cut into units
 // (frame group, tile, segment of G sensors); units of all instances form one
 // sequence that the launch splits into contiguous ranges, one per CTA.
@@ -80,6 +87,9 @@ int gather_threads(const GatherConfig& c);
 int gather_resident_ctas(const GatherConfig& c, int fmt, int Wst, int n_sm);
 
 cudaError_t launch_preprocess(const PreParams& p, cudaStream_t st);
+cudaError_t launch_preprocess_multi(const PreMultiParams& p, cudaStream_t st);
+const void* gather_kernel_func(const GatherConfig& c, int fmt);
+const void* preprocess_multi_func(int dtype, int fmt, int FB);
 cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
                           cudaStream_t st);
 cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t st);

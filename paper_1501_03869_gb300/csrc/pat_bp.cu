@@ -17,13 +17,11 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pat_bp.h"
-#include "kernels.cuh"
-#include "table.h"
+#include "handle.h"
 
 using namespace patbp;
 
-namespace {
+namespace patbp {
 
 thread_local std::string g_last_error;
 
@@ -37,60 +35,7 @@ pat_status cuda_fail(cudaError_t e, const char* what) {
   return PAT_ERR_CUDA;
 }
 
-#define PAT_CUDA(call)                                     \
-  do {                                                     \
-    cudaError_t e_ = (call);                               \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
-  } while (0)
-
-int round_up(int x, int m) { return (x + m - 1) / m * m; }
-
-}  // namespace
-
-struct pat_bp_s {
-  int device = 0;
-  int n_sm = 0;
-  GridDesc g;
-  int ns = 0, ns_pad = 0, nt = 0, nt_pad = 0;
-  double dt = 0.0;
-  unsigned flags = 0;
-  bool compact = false;
-  int P = 128, SW = 4, n_tiles = 0, W = 0;
-  int G = 64, n_seg = 1;              // sensors per segment, segments per tile
-  int64_t n_pix = 0, grid_total = 0, out_stride = 0;
-  int n_zero_runs = 0;
-  double build_seconds = 0.0;
-  std::vector<uint16_t> win_len;      // host copy of the window lengths [tile][sensor]
-  int pre_frames = 0;                 // frames held by the integrand buffer
-  int pre_fmt = 0;                    // their storage format
-  int pre_fb = 1;                     // their frames per group
-  int resident[4][3][2] = {};         // cached CTAs per launch by (FB index, format, S == 8)
-  int wst_cache[33] = {0};            // stage window bound per sensors-per-stage
-  float* d_u = nullptr;
-  int32_t* d_base = nullptr;
-  int32_t* d_slot = nullptr;
-  int32_t* d_zero_runs = nullptr;
-  float* d_w = nullptr;
-  int* d_status = nullptr;
-  unsigned* d_sched = nullptr;        // gather unit tickets (self-resetting)
-  void* d_b = nullptr;
-  size_t b_cap = 0;
-  float* d_m = nullptr;
-  size_t m_cap = 0;
-  float* d_part = nullptr;            // segment partial sums (scratch)
-  size_t part_cap = 0;
-  int* d_counter = nullptr;           // per (frame group, tile) segment counters
-  size_t counter_cap = 0;
-  // staging of pat_bp_reconstruct_host
-  cudaStream_t own_stream = nullptr;
-  void* d_sig = nullptr;
-  size_t sig_cap = 0;
-  float* d_scales = nullptr;
-  size_t scales_cap = 0;
-  float* d_out = nullptr;
-  size_t out_cap = 0;
-  std::mutex mu;
-};
+}  // namespace patbp
 
 extern "C" const char* pat_status_str(pat_status s) {
   switch (s) {
@@ -189,6 +134,7 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
   cudaDeviceProp prop;
   PAT_CUDA(cudaGetDeviceProperties(&prop, h->device));
   h->n_sm = prop.multiProcessorCount;
+  h->max_smem = int(prop.sharedMemPerBlockOptin);
   h->g = g;
   h->ns = n_sensors;
   h->ns_pad = round_up(n_sensors, 4);
@@ -261,13 +207,15 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
   return PAT_OK;
 }
 
-static int fmt_for(pat_dtype dt) {
-  return dt == PAT_F32 ? kBF32 : (dt == PAT_BF16 ? kBBF16P : kBF16P);
-}
+namespace patbp {
 
-static int frames_per_group(int n_frames) {
+int fmt_for(pat_dtype dt) { return dt == PAT_F32 ? kBF32 : (dt == PAT_BF16 ? kBBF16P : kBF16P); }
+
+int frames_per_group(int n_frames) {
   return n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1));
 }
+
+int fb_index(int FB) { return FB == 1 ? 0 : (FB == 2 ? 1 : (FB == 4 ? 2 : 3)); }
 
 static pat_status grow_zeroed(void** p, size_t* cap, size_t need, const char* what) {
   if (need <= *cap) return PAT_OK;
@@ -280,8 +228,7 @@ static pat_status grow_zeroed(void** p, size_t* cap, size_t need, const char* wh
   return PAT_OK;
 }
 
-static pat_status ensure_buffers(pat_bp_t h, int n_frames) {
-  const int FB = frames_per_group(n_frames);
+pat_status ensure_buffers_fb(pat_bp_t h, int n_frames, int FB) {
   const size_t n_fg = size_t((n_frames + FB - 1) / FB);
   pat_status st;
   const size_t b_need = (n_fg * h->ns * h->nt_pad + kTailRows) * FB * 4;
@@ -304,7 +251,7 @@ static pat_status ensure_buffers(pat_bp_t h, int n_frames) {
 
 // Largest sum of window lengths over the S-sensor stages of any tile: the
 // window rows one pipeline stage must hold.
-static int stage_window(pat_bp_t h, int S) {
+int stage_window(pat_bp_t h, int S) {
   if (S >= 1 && S <= 32 && h->wst_cache[S]) return h->wst_cache[S];
   int best = 8;
   for (int t = 0; t < h->n_tiles; ++t) {
@@ -320,22 +267,113 @@ static int stage_window(pat_bp_t h, int S) {
   return best;
 }
 
-// Launch shape for a frame count: frames per unit, sensors per stage, stages.
-static GatherConfig pick_config(pat_bp_t h, int n_frames, int* wst) {
+// Launch shape under a shared-memory budget: as many stages as fit (2..6),
+// fewer sensors per stage if even two stages do not fit.
+GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
   GatherConfig c;
   c.P = h->P;
   c.SW = h->SW;
-  c.FB = frames_per_group(n_frames);
-  c.S = c.FB == 1 ? 16 : 8;
-  const size_t budget = c.FB == 1 ? 55 * 1024 : 100 * 1024;
+  c.FB = FB;
+  c.S = S;
   c.stages = 6;
   for (;;) {
     *wst = stage_window(h, c.S);
     while (c.stages > 2 && gather_smem_bytes(c, *wst) > budget) --c.stages;
-    if (gather_smem_bytes(c, *wst) <= budget || c.S <= 8) break;
-    c.S -= 8;
+    if (gather_smem_bytes(c, *wst) <= budget || c.S <= 4) break;
+    c.S = c.S > 8 ? c.S - 8 : 4;
   }
   return c;
+}
+
+// Launch shape for a frame count: the autotuned one when the handle has it,
+// else frames per unit by count, 16 (1 frame) or 8 sensors per stage and a
+// budget of four (1 frame) or two CTAs per SM.  When the stage windows are too
+// long for that budget, the budget grows to the device limit and then fewer
+// frames share a unit.  No choice here changes the summation order.
+GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst) {
+  const size_t limit = size_t(h->max_smem);
+  for (int FB = frames_per_group(n_frames); FB >= 1; FB /= 2) {
+    const int fi = fb_index(FB);
+    GatherConfig c;
+    if (h->tuned_S[fi][fmt] > 0)
+      c = config_for(h, FB, h->tuned_S[fi][fmt], size_t(h->tuned_budget_kb[fi][fmt]) * 1024, wst);
+    else
+      c = config_for(h, FB, FB == 1 ? 16 : 8, FB == 1 ? 55 * 1024 : 100 * 1024, wst);
+    if (gather_smem_bytes(c, *wst) <= limit) return c;
+    c = config_for(h, FB, 8, limit, wst);
+    if (gather_smem_bytes(c, *wst) <= limit) return c;
+  }
+  return config_for(h, 1, 4, limit, wst);  // may not fit: the launch reports it
+}
+
+PreParams make_pre(pat_bp_t h, const void* sig, pat_dtype dtype, const float* scales, int n_frames,
+                   int FB) {
+  PreParams pp;
+  pp.sig = sig;
+  pp.scales = scales;
+  pp.weights = h->d_w;
+  pp.b = h->d_b;
+  pp.m = h->d_m;
+  pp.dtype = int(dtype);
+  pp.fmt = fmt_for(dtype);
+  pp.FB = FB;
+  pp.n_sensors = h->ns;
+  pp.n_sensors_pad = h->ns_pad;
+  pp.n_t = h->nt;
+  pp.n_t_pad = h->nt_pad;
+  pp.n_frames = n_frames;
+  return pp;
+}
+
+InstDesc make_desc(pat_bp_t h, float* out, int n_frames, int FB, int wst) {
+  InstDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.u = h->d_u;
+  d.base = h->d_base;
+  d.slot = h->d_slot;
+  d.zero_runs = h->d_zero_runs;
+  d.n_zero_runs = h->n_zero_runs;
+  d.b = h->d_b;
+  d.m = h->d_m;
+  d.out = out;
+  d.part = h->d_part;
+  d.counter = h->d_counter;
+  d.out_stride = h->out_stride;
+  d.unit_begin = 0;
+  d.n_sensors = h->ns;
+  d.n_sensors_pad = h->ns_pad;
+  d.n_t_pad = h->nt_pad;
+  d.n_tiles = h->n_tiles;
+  d.n_frames = n_frames;
+  d.n_fg = (n_frames + FB - 1) / FB;
+  d.n_seg = h->n_seg;
+  d.G = h->G;
+  d.Wst = wst;
+  return d;
+}
+
+int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm) {
+  struct Key {
+    int P, FB, SW, S, stages, fmt, wst;
+  };
+  static std::mutex mu;
+  static std::vector<std::pair<Key, int>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& e : cache) {
+    const Key& k = e.first;
+    if (k.P == c.P && k.FB == c.FB && k.SW == c.SW && k.S == c.S && k.stages == c.stages &&
+        k.fmt == fmt && k.wst == wst)
+      return e.second;
+  }
+  const int r = gather_resident_ctas(c, fmt, wst, n_sm);
+  cache.push_back({Key{c.P, c.FB, c.SW, c.S, c.stages, fmt, wst}, r});
+  return r;
+}
+
+}  // namespace patbp
+
+static pat_status ensure_buffers(pat_bp_t h, int n_frames) {
+  return ensure_buffers_fb(h, n_frames, frames_per_group(n_frames));
 }
 
 extern "C" pat_status pat_bp_reserve(pat_bp_t h, int max_frames, pat_dtype dtype) {
@@ -353,22 +391,11 @@ static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dty
   if (dtype != PAT_F32 && dtype != PAT_BF16 && dtype != PAT_F16)
     return fail(PAT_ERR_INVALID, "unknown dtype");
   if (dtype != PAT_F32 && !scales_dev) return fail(PAT_ERR_INVALID, "16-bit signals need scales");
-  pat_status st = ensure_buffers(h, n_frames);
+  int wst = 0;
+  const int FB = pick_config(h, n_frames, fmt_for(dtype), &wst).FB;
+  pat_status st = ensure_buffers_fb(h, n_frames, FB);
   if (st != PAT_OK) return st;
-  PreParams pp;
-  pp.sig = signals_dev;
-  pp.scales = scales_dev;
-  pp.weights = h->d_w;
-  pp.b = h->d_b;
-  pp.m = h->d_m;
-  pp.dtype = int(dtype);
-  pp.fmt = fmt_for(dtype);
-  pp.n_sensors = h->ns;
-  pp.n_sensors_pad = h->ns_pad;
-  pp.n_t = h->nt;
-  pp.n_t_pad = h->nt_pad;
-  pp.n_frames = n_frames;
-  pp.FB = frames_per_group(n_frames);
+  const PreParams pp = make_pre(h, signals_dev, dtype, scales_dev, n_frames, FB);
   cudaError_t e = launch_preprocess(pp, stream);
   if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
   h->pre_frames = n_frames;
@@ -382,32 +409,12 @@ static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaSt
   if (n_frames < 1 || n_frames != h->pre_frames)
     return fail(PAT_ERR_INVALID, "gather needs the preprocess of the same n_frames first");
   int wst = 0;
-  GatherConfig c = pick_config(h, n_frames, &wst);
+  const GatherConfig c = pick_config(h, n_frames, h->pre_fmt, &wst);
   if (c.FB != h->pre_fb) return fail(PAT_ERR_INVALID, "frame grouping changed since preprocess");
   StreamParams sp;
   std::memset(&sp, 0, sizeof(sp));
-  InstDesc& d = sp.inst[0];
-  d.u = h->d_u;
-  d.base = h->d_base;
-  d.slot = h->d_slot;
-  d.zero_runs = h->d_zero_runs;
-  d.n_zero_runs = h->n_zero_runs;
-  d.b = h->d_b;
-  d.m = h->d_m;
-  d.out = out_dev;
-  d.part = h->d_part;
-  d.counter = h->d_counter;
-  d.out_stride = h->out_stride;
-  d.unit_begin = 0;
-  d.n_sensors = h->ns;
-  d.n_sensors_pad = h->ns_pad;
-  d.n_t_pad = h->nt_pad;
-  d.n_tiles = h->n_tiles;
-  d.n_frames = n_frames;
-  d.n_fg = (n_frames + c.FB - 1) / c.FB;
-  d.n_seg = h->n_seg;
-  d.G = h->G;
-  d.Wst = wst;
+  sp.inst[0] = make_desc(h, out_dev, n_frames, c.FB, wst);
+  const InstDesc& d = sp.inst[0];
   sp.n_inst = 1;
   sp.n_units = int64_t(d.n_fg) * d.n_tiles * d.n_seg;
   sp.S = c.S;
@@ -416,9 +423,7 @@ static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaSt
   sp.status = h->d_status;
   sp.sched = h->d_sched;
   sp.timeout_ns = 2000000000ull;
-  const int fbi = c.FB == 1 ? 0 : (c.FB == 2 ? 1 : (c.FB == 4 ? 2 : 3));
-  int& res = h->resident[fbi][h->pre_fmt][c.S == 8 ? 1 : 0];
-  if (res == 0) res = gather_resident_ctas(c, h->pre_fmt, wst, h->n_sm);
+  const int res = resident_ctas(c, h->pre_fmt, wst, h->n_sm);
   if (res <= 0) return fail(PAT_ERR_CUDA, "gather kernel does not fit on the device");
   const int grid = int(std::min<int64_t>(sp.n_units, res));
   cudaError_t e = launch_gather(c, h->pre_fmt, sp, grid, stream);

@@ -1,0 +1,522 @@
+// plan.cu -- many instances in one persistent launch (include/pat_bp.h, plans).
+//
+// Every instance (one speed map's table, Sec. III) contributes its units to
+// one gather launch; one preprocessing launch forms the Eq. (BP) integrand of
+// all instances first.  A plan can replay both launches as a CUDA graph whose
+// kernel-node parameters are refreshed per execution, and can time candidate
+// launch shapes once (autotuning).  None of the shape choices changes the
+// order in which a pixel's sensor terms are summed, so results never depend on
+// the shape, the graph or the other instances.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+
+using namespace patbp;
+
+struct pat_plan_s {
+  std::vector<pat_bp_t> hs;
+  std::vector<int> frames;
+  pat_dtype dtype = PAT_F32;
+  int fmt = 0;
+  unsigned flags = 0;
+  int device = 0, n_sm = 0, P = 128, SW = 4;
+  // launch shape
+  int FB = 1, S = 16, budget_kb = 55;
+  GatherConfig cfg;
+  int wst = 8;
+  int grid = 0;
+  int64_t n_units = 0;
+  bool tuned = false;
+  double tune_ms = 0.0;
+  // device words owned by the plan
+  int* d_status = nullptr;
+  unsigned* d_sched = nullptr;
+  // parameter blocks (refreshed per execution)
+  std::unique_ptr<PreMultiParams> pre;
+  std::unique_ptr<StreamParams> gat;
+  // graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t pre_node = nullptr, gat_node = nullptr;
+  std::mutex mu;
+};
+
+namespace {
+
+pat_status plan_shape(pat_plan_t pl, int FB, int S, int budget_kb) {
+  pl->FB = FB;
+  pl->S = S;
+  pl->budget_kb = budget_kb;
+  int wst = 8;
+  for (pat_bp_t h : pl->hs) wst = std::max(wst, stage_window(h, S));
+  // one shape for all instances: the largest stage window decides the stages
+  GatherConfig c;
+  c.P = pl->P;
+  c.SW = pl->SW;
+  c.FB = FB;
+  c.S = S;
+  c.stages = 6;
+  const size_t budget = std::min(size_t(budget_kb) * 1024, size_t(pl->hs[0]->max_smem));
+  while (c.stages > 2 && gather_smem_bytes(c, wst) > budget) --c.stages;
+  if (gather_smem_bytes(c, wst) > budget)
+    return fail(PAT_ERR_CUDA, "stage windows do not fit in shared memory for this shape");
+  pl->cfg = c;
+  pl->wst = wst;
+  for (size_t i = 0; i < pl->hs.size(); ++i) {
+    pat_status st = ensure_buffers_fb(pl->hs[i], pl->frames[i], FB);
+    if (st != PAT_OK) return st;
+  }
+  // unit ranges and preprocessing CTA ranges
+  StreamParams& sp = *pl->gat;
+  PreMultiParams& pm = *pl->pre;
+  std::memset(&sp, 0, sizeof(sp));
+  std::memset(&pm, 0, sizeof(pm));
+  int64_t units = 0, ctas = 0;
+  for (size_t i = 0; i < pl->hs.size(); ++i) {
+    pat_bp_t h = pl->hs[i];
+    sp.inst[i] = make_desc(h, nullptr, pl->frames[i], FB, wst);
+    sp.inst[i].unit_begin = units;
+    units += int64_t(sp.inst[i].n_fg) * sp.inst[i].n_tiles * sp.inst[i].n_seg;
+    pm.inst[i] = make_pre(h, nullptr, pl->dtype, nullptr, pl->frames[i], FB);
+    pm.cta_begin[i] = ctas;
+    ctas += int64_t(h->ns) * sp.inst[i].n_fg;
+  }
+  pm.cta_begin[pl->hs.size()] = ctas;
+  pm.n_inst = int(pl->hs.size());
+  pm.dtype = int(pl->dtype);
+  pm.fmt = pl->fmt;
+  pm.FB = FB;
+  sp.n_inst = int(pl->hs.size());
+  sp.n_units = units;
+  sp.S = pl->cfg.S;
+  sp.stages = pl->cfg.stages;
+  sp.Wst = wst;
+  sp.status = pl->d_status;
+  sp.sched = pl->d_sched;
+  sp.timeout_ns = 2000000000ull;
+  pl->n_units = units;
+  const int res = resident_ctas(pl->cfg, pl->fmt, wst, pl->n_sm);
+  if (res <= 0) return fail(PAT_ERR_CUDA, "gather kernel does not fit on the device");
+  pl->grid = int(std::min<int64_t>(units, res));
+  if (ctas > 0x7fffffff) return fail(PAT_ERR_INVALID, "too many preprocessing rows in one plan");
+  return PAT_OK;
+}
+
+void fill_pointers(pat_plan_t pl, const void* const* sig, const float* const* scales,
+                   float* const* outs) {
+  for (size_t i = 0; i < pl->hs.size(); ++i) {
+    pl->pre->inst[i].sig = sig[i];
+    pl->pre->inst[i].scales = scales ? scales[i] : nullptr;
+    pl->gat->inst[i].out = outs[i];
+  }
+}
+
+pat_status launch_both(pat_plan_t pl, cudaStream_t st) {
+  cudaError_t e = launch_preprocess_multi(*pl->pre, st);
+  if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
+  e = launch_gather(pl->cfg, pl->fmt, *pl->gat, pl->grid, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+  return PAT_OK;
+}
+
+void drop_graph(pat_plan_t pl) {
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  pl->exec = nullptr;
+  pl->graph = nullptr;
+  pl->pre_node = pl->gat_node = nullptr;
+}
+
+}  // namespace
+
+namespace {
+
+// Point every descriptor at the handles' current buffers (a handle's own
+// calls may have grown them since the plan was shaped).
+pat_status refresh_buffers(pat_plan_t pl) {
+  for (size_t i = 0; i < pl->hs.size(); ++i) {
+    pat_bp_t h = pl->hs[i];
+    pat_status st = ensure_buffers_fb(h, pl->frames[i], pl->FB);
+    if (st != PAT_OK) return st;
+    pl->pre->inst[i].b = h->d_b;
+    pl->pre->inst[i].m = h->d_m;
+    pl->gat->inst[i].b = h->d_b;
+    pl->gat->inst[i].m = h->d_m;
+    pl->gat->inst[i].part = h->d_part;
+    pl->gat->inst[i].counter = h->d_counter;
+  }
+  return PAT_OK;
+}
+
+pat_status capture(pat_plan_t pl) {
+  if (!pl->cap_stream) PAT_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+  PAT_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+  pat_status st = launch_both(pl, pl->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+  if (st != PAT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+  size_t n = 0;
+  PAT_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  PAT_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+  const void* fpre = preprocess_multi_func(int(pl->dtype), pl->fmt, pl->FB);
+  const void* fgat = gather_kernel_func(pl->cfg, pl->fmt);
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    PAT_CUDA(cudaGraphNodeGetType(nd, &t));
+    if (t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    PAT_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
+    if (kp.func == fpre) pl->pre_node = nd;
+    if (kp.func == fgat) pl->gat_node = nd;
+  }
+  if (!pl->pre_node || !pl->gat_node) {
+    cudaGraphDestroy(g);
+    return fail(PAT_ERR_CUDA, "captured graph lacks the expected kernels");
+  }
+  pl->graph = g;
+  PAT_CUDA(cudaGraphInstantiate(&pl->exec, g, 0));
+  return PAT_OK;
+}
+
+pat_status refresh_graph(pat_plan_t pl) {
+  void* pre_args[1] = {pl->pre.get()};
+  void* gat_args[1] = {pl->gat.get()};
+  cudaKernelNodeParams kp;
+  PAT_CUDA(cudaGraphKernelNodeGetParams(pl->pre_node, &kp));
+  kp.kernelParams = pre_args;
+  kp.extra = nullptr;
+  PAT_CUDA(cudaGraphExecKernelNodeSetParams(pl->exec, pl->pre_node, &kp));
+  PAT_CUDA(cudaGraphKernelNodeGetParams(pl->gat_node, &kp));
+  kp.kernelParams = gat_args;
+  kp.extra = nullptr;
+  PAT_CUDA(cudaGraphExecKernelNodeSetParams(pl->exec, pl->gat_node, &kp));
+  return PAT_OK;
+}
+
+// Shapes chosen earlier in this process (and, with PAT_TUNE_CACHE set, in a
+// text file of "signature FB S budget_kb" lines), keyed by the plan's shape.
+std::mutex g_tune_mu;
+std::map<std::string, std::vector<int>> g_tune;
+
+std::string signature(pat_plan_t pl, bool fixed_fb) {
+  std::string s = "sm" + std::to_string(pl->n_sm) + ".dt" + std::to_string(int(pl->dtype)) +
+                  (fixed_fb ? ".fb" + std::to_string(pl->FB) : std::string(".fbany"));
+  for (size_t i = 0; i < pl->hs.size(); ++i) {
+    pat_bp_t h = pl->hs[i];
+    s += "|" + std::to_string(h->ns) + "x" + std::to_string(h->nt) + "x" + std::to_string(h->n_tiles) +
+         "x" + std::to_string(h->W) + "f" + std::to_string(pl->frames[i]);
+  }
+  return s;
+}
+
+void tune_file_load() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char* path = std::getenv("PAT_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char key[4096];
+  int fb, s, b;
+  while (std::fscanf(f, "%4095s %d %d %d", key, &fb, &s, &b) == 4) g_tune[key] = {fb, s, b};
+  std::fclose(f);
+}
+
+void tune_file_store(const std::string& key, int fb, int s, int b) {
+  const char* path = std::getenv("PAT_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d\n", key.c_str(), fb, s, b);
+  std::fclose(f);
+}
+
+// Times every candidate shape on the given inputs and keeps the fastest.
+pat_status autotune(pat_plan_t pl, const void* const* sig, const float* const* scales,
+                    float* const* outs, cudaStream_t st, bool fixed_fb) {
+  const std::string key = signature(pl, fixed_fb);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_file_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      pat_status s = plan_shape(pl, it->second[0], it->second[1], it->second[2]);
+      if (s == PAT_OK) pl->tuned = true;
+      return s;
+    }
+  }
+  int max_f = 1;
+  for (int f : pl->frames) max_f = std::max(max_f, f);
+  std::vector<int> fbs;
+  if (fixed_fb) {
+    fbs.push_back(pl->FB);
+  } else {
+    for (int fb = 1; fb <= 8; fb *= 2) {
+      fbs.push_back(fb);
+      if (fb >= max_f) break;
+    }
+  }
+  const int Ss[4] = {4, 8, 16, 32};
+  const int budgets[4] = {55, 72, 110, pl->hs[0]->max_smem / 1024};
+  cudaEvent_t e0, e1;
+  PAT_CUDA(cudaEventCreate(&e0));
+  PAT_CUDA(cudaEventCreate(&e1));
+  double best = 1e30;
+  int bfb = pl->FB, bs = pl->S, bb = pl->budget_kb;
+  pat_status st_all = PAT_OK;
+  for (int fb : fbs)
+    for (int S : Ss)
+      for (int b : budgets) {
+        if (S == 4 && b != budgets[3]) continue;  // 4 sensors per stage only as a last resort
+        pat_status s = plan_shape(pl, fb, S, b);
+        if (s != PAT_OK) continue;
+        if ((s = refresh_buffers(pl)) != PAT_OK) {
+          st_all = s;
+          continue;
+        }
+        fill_pointers(pl, sig, scales, outs);
+        if (launch_both(pl, st) != PAT_OK) continue;  // warm-up
+        cudaEventRecord(e0, st);
+        if (launch_both(pl, st) != PAT_OK) continue;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return cuda_fail(cudaGetLastError(), "autotune run");
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          bfb = fb;
+          bs = S;
+          bb = b;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best >= 1e30) return st_all != PAT_OK ? st_all : fail(PAT_ERR_CUDA, "no launch shape ran");
+  pat_status s = plan_shape(pl, bfb, bs, bb);
+  if (s != PAT_OK) return s;
+  pl->tuned = true;
+  pl->tune_ms = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {bfb, bs, bb};
+  tune_file_store(key, bfb, bs, bb);
+  return PAT_OK;
+}
+
+}  // namespace
+
+static pat_status plan_new(const pat_bp_t* handles, const int* n_frames, int n, pat_dtype dtype,
+                           unsigned flags, bool own_words, pat_plan_t* out) {
+  if (!out) return fail(PAT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!handles || !n_frames || n < 1 || n > kMaxInst)
+    return fail(PAT_ERR_INVALID, "a plan holds 1..64 handles");
+  if (dtype != PAT_F32 && dtype != PAT_BF16 && dtype != PAT_F16) return fail(PAT_ERR_INVALID, "dtype");
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i]) return fail(PAT_ERR_INVALID, "NULL handle");
+    if (n_frames[i] < 1 || n_frames[i] > 65535) return fail(PAT_ERR_INVALID, "n_frames must be 1..65535");
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(PAT_ERR_INVALID, "a handle appears twice in one plan");
+    if (handles[i]->device != handles[0]->device || handles[i]->P != handles[0]->P)
+      return fail(PAT_ERR_INVALID, "plan handles must share the device and the tile size");
+  }
+  std::unique_ptr<pat_plan_s> pl(new (std::nothrow) pat_plan_s());
+  if (!pl) return fail(PAT_ERR_OOM, "plan");
+  pl->hs.assign(handles, handles + n);
+  pl->frames.assign(n_frames, n_frames + n);
+  pl->dtype = dtype;
+  pl->fmt = fmt_for(dtype);
+  pl->flags = flags;
+  pl->device = handles[0]->device;
+  pl->n_sm = handles[0]->n_sm;
+  pl->P = handles[0]->P;
+  pl->SW = handles[0]->SW;
+  pl->pre.reset(new (std::nothrow) PreMultiParams());
+  pl->gat.reset(new (std::nothrow) StreamParams());
+  if (!pl->pre || !pl->gat) return fail(PAT_ERR_OOM, "plan parameters");
+  PAT_CUDA(cudaSetDevice(pl->device));
+  if (own_words) {
+    if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&pl->d_sched, 4 * sizeof(unsigned)) != cudaSuccess) {
+      cudaFree(pl->d_status);
+      return fail(PAT_ERR_OOM, "plan words");
+    }
+    PAT_CUDA(cudaMemset(pl->d_status, 0, sizeof(int)));
+    PAT_CUDA(cudaMemset(pl->d_sched, 0, 4 * sizeof(unsigned)));
+  } else {
+    pl->d_status = handles[0]->d_status;
+    pl->d_sched = handles[0]->d_sched;
+  }
+  std::vector<int> fr(pl->frames);
+  std::sort(fr.begin(), fr.end());
+  // default shape: frames per unit from the median frame count; if the stage
+  // windows do not fit, fewer sensors per stage, more shared memory, then
+  // fewer frames per unit
+  pat_status st = PAT_ERR_CUDA;
+  const int limit_kb = handles[0]->max_smem / 1024;
+  for (int FB = frames_per_group(fr[fr.size() / 2]); FB >= 1 && st != PAT_OK; FB /= 2) {
+    const int tries[3][2] = {{FB == 1 ? 16 : 8, FB == 1 ? 55 : 100}, {8, limit_kb}, {4, limit_kb}};
+    for (const auto& t : tries) {
+      st = plan_shape(pl.get(), FB, t[0], t[1]);
+      if (st == PAT_OK) break;
+    }
+  }
+  if (st != PAT_OK) {
+    if (own_words) {
+      cudaFree(pl->d_status);
+      cudaFree(pl->d_sched);
+    }
+    return st;
+  }
+  if (!own_words) pl->flags |= 0x80000000u;  // marks borrowed device words
+  *out = pl.release();
+  return PAT_OK;
+}
+
+static pat_status plan_run(pat_plan_t pl, const void* const* sig, const float* const* scales,
+                           float* const* outs, cudaStream_t stream) {
+  if (!sig || !outs) return fail(PAT_ERR_INVALID, "signals/outs NULL");
+  for (size_t i = 0; i < pl->hs.size(); ++i) {
+    if (!sig[i] || !outs[i]) return fail(PAT_ERR_INVALID, "NULL signal or output pointer");
+    if (pl->dtype != PAT_F32 && (!scales || !scales[i]))
+      return fail(PAT_ERR_INVALID, "16-bit signals need scales");
+  }
+  PAT_CUDA(cudaSetDevice(pl->device));
+  pat_status st;
+  if ((pl->flags & PAT_PLAN_AUTOTUNE) && !pl->tuned) {
+    if ((st = autotune(pl, sig, scales, outs, stream, false)) != PAT_OK) return st;
+    drop_graph(pl);
+  }
+  if ((st = refresh_buffers(pl)) != PAT_OK) return st;
+  fill_pointers(pl, sig, scales, outs);
+  if (!(pl->flags & PAT_PLAN_GRAPH)) return launch_both(pl, stream);
+  if (!pl->exec) {
+    if ((st = capture(pl)) != PAT_OK) return st;
+  } else if ((st = refresh_graph(pl)) != PAT_OK) {
+    return st;
+  }
+  PAT_CUDA(cudaGraphLaunch(pl->exec, stream));
+  return PAT_OK;
+}
+
+static void plan_free(pat_plan_t pl) {
+  if (!pl) return;
+  cudaSetDevice(pl->device);
+  cudaDeviceSynchronize();
+  drop_graph(pl);
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  if (!(pl->flags & 0x80000000u)) {
+    cudaFree(pl->d_status);
+    cudaFree(pl->d_sched);
+  }
+  delete pl;
+}
+
+extern "C" pat_status pat_plan_create(const pat_bp_t* handles, const int* n_frames, int n,
+                                      pat_dtype dtype, unsigned flags, pat_plan_t* out) {
+  return plan_new(handles, n_frames, n, dtype, flags & (PAT_PLAN_AUTOTUNE | PAT_PLAN_GRAPH), true, out);
+}
+
+extern "C" pat_status pat_plan_execute(pat_plan_t plan, const void* const* signals_dev,
+                                       const float* const* scales_dev, float* const* outs_dev,
+                                       pat_stream_t stream) {
+  if (!plan) return fail(PAT_ERR_INVALID, "NULL plan");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  return plan_run(plan, signals_dev, scales_dev, outs_dev, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pat_status pat_plan_sync(pat_plan_t plan, pat_stream_t stream) {
+  if (!plan) return fail(PAT_ERR_INVALID, "NULL plan");
+  PAT_CUDA(cudaSetDevice(plan->device));
+  PAT_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int flag = 0;
+  PAT_CUDA(cudaMemcpy(&flag, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!flag) return PAT_OK;
+  PAT_CUDA(cudaMemset(plan->d_status, 0, sizeof(int)));
+  PAT_CUDA(cudaMemset(plan->d_sched, 0, 4 * sizeof(unsigned)));
+  for (pat_bp_t h : plan->hs)
+    if (h->d_counter) PAT_CUDA(cudaMemset(h->d_counter, 0, h->counter_cap));
+  return fail(flag & kStatusTimeout ? PAT_ERR_TIMEOUT : PAT_ERR_CUDA,
+              flag & kStatusTimeout ? "a device wait ran out of time" : "bad launch configuration");
+}
+
+extern "C" pat_status pat_plan_info(pat_plan_t plan, pat_plan_info_t* info) {
+  if (!plan || !info) return fail(PAT_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  info->n_inst = int(plan->hs.size());
+  info->frames_per_unit = plan->FB;
+  info->sensors_per_stage = plan->cfg.S;
+  info->stages = plan->cfg.stages;
+  info->smem_budget_kb = plan->budget_kb;
+  info->grid = plan->grid;
+  info->n_units = plan->n_units;
+  info->tuned = plan->tuned ? 1 : 0;
+  info->graph = plan->exec ? 1 : 0;
+  info->tune_ms = plan->tune_ms;
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_plan_destroy(pat_plan_t plan) {
+  plan_free(plan);
+  return PAT_OK;
+}
+
+extern "C" pat_status pat_bp_reconstruct_multi(const pat_bp_t* handles, const void* const* signals_dev,
+                                               pat_dtype dtype, const float* const* scales_dev,
+                                               const int* n_frames, float* const* outs_dev, int n,
+                                               pat_stream_t stream) {
+  pat_plan_t pl = nullptr;
+  pat_status st = plan_new(handles, n_frames, n, dtype, 0, false, &pl);
+  if (st != PAT_OK) return st;
+  st = plan_run(pl, signals_dev, scales_dev, outs_dev, static_cast<cudaStream_t>(stream));
+  // the plan's parameter blocks were copied at launch; its device words are
+  // the first handle's, so nothing in flight depends on the plan object
+  drop_graph(pl);
+  delete pl;
+  return st;
+}
+
+extern "C" pat_status pat_bp_autotune(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                                      const float* scales_dev, int n_frames, float* out_dev,
+                                      pat_stream_t stream) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  pat_plan_t pl = nullptr;
+  pat_status st = plan_new(&h, &n_frames, 1, dtype, 0, false, &pl);
+  if (st != PAT_OK) return st;
+  pl->FB = frames_per_group(n_frames);
+  const void* sig[1] = {signals_dev};
+  const float* sc[1] = {scales_dev};
+  float* outs[1] = {out_dev};
+  st = autotune(pl, sig, dtype == PAT_F32 ? (scales_dev ? sc : nullptr) : sc, outs,
+                static_cast<cudaStream_t>(stream), true);
+  if (st == PAT_OK) {
+    const int fi = fb_index(pl->FB);
+    h->tuned_S[fi][pl->fmt] = pl->S;
+    h->tuned_budget_kb[fi][pl->fmt] = pl->budget_kb;
+  }
+  cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  drop_graph(pl);
+  delete pl;
+  return st;
+}

@@ -421,7 +421,8 @@ def config3(n_frames=64, arrivals=None):
 def config4_instance(inst, noise=0.01, arrivals=None, n_frames=None):
     """One uneven instance: N ~ U{96..384}, dx ~ U[0.1, 0.2] mm, ns ~ U{128..1024},
     nt ~ U{1024..4096}, F ~ U{1..16}; skull like config 2 scaled to N, ring at
-    0.47 N, dt such that nt dt >= 1.5 d / c0; mask r < 0.32 N."""
+    0.47 N, dt such that nt dt >= 1.5 d / c0; mask r < 0.32 N; 5 disc absorbers
+    shared by the frames, amplitudes and noise drawn per frame."""
     rng = rng_for(4, inst, 0, 0)
     N = int(rng.integers(96, 385))
     dx = float(rng.uniform(0.1e-3, 0.2e-3))
@@ -440,14 +441,18 @@ def config4_instance(inst, noise=0.01, arrivals=None, n_frames=None):
     mask = (node_radius_px(shape) < 0.32 * N).astype(np.uint8)
     if n_frames is not None:
         F = n_frames
+    # the frames of one instance share the absorber positions (one set of
+    # arrival times) and differ in amplitudes and noise
+    r2 = rng_for(4, inst, 0, 2)
+    c = _random_points_in_disc(r2, 5, 0.3 * N * dx)
+    r = r2.uniform(1.0, 3.0, 5) * dx
+    T0 = (arrivals or straight_ray_arrivals)(speed, dx, origin, c, sensors)
+    ca = local_speed(speed, dx, origin, c)
     sig, p0 = [], []
     for f in range(F):
-        r2 = rng_for(4, inst, f, 2)
-        c = _random_points_in_disc(r2, 5, 0.3 * N * dx)
-        r = r2.uniform(1.0, 3.0, 5) * dx
-        a = r2.uniform(0.5, 1.0, 5)
-        sig.append(render_signals(speed, dx, origin, sensors, c, r, a, dt, nt, noise, r2,
-                                  arrivals))
+        rf = rng_for(4, inst, f, 3)
+        a = rf.uniform(0.5, 1.0, 5)
+        sig.append(_pulses(T0, ca, r, a, dt, nt, noise, rf))
         p0.append(phantom_discs(shape, dx, origin, c, r, a))
     return Workload(f"c4_{inst}", speed, dx, origin, sensors, mask, dt, nt, np.stack(sig),
                     np.stack(p0))
