@@ -61,6 +61,8 @@ typedef void* pat_stream_t; /* a cudaStream_t; NULL = legacy default stream */
                                      instead of the dense [F][grid] image        */
 #define PAT_FLAG_TILE_128 0x10u   /* force 128 pixels per tile                   */
 #define PAT_FLAG_TILE_256 0x20u   /* force 256 pixels per tile                   */
+#define PAT_FLAG_HOST_MIRROR 0x100u /* keep a pinned host copy of the table so the
+                                       device copy can be evicted and restored    */
 
 /* Read-only facts about a handle (pat_bp_info). */
 typedef struct {
@@ -152,6 +154,15 @@ pat_status pat_bp_info(pat_bp_t h, pat_bp_info_t* info);
  * may be NULL.  u + base is T/dt; entries out of the record hold 1e30. */
 pat_status pat_bp_table(pat_bp_t h, float* u_host, int32_t* base_host, int32_t* pix_host);
 
+/* pat_bp_evict -- free the handle's device table and working buffers (needs
+ * PAT_FLAG_HOST_MIRROR); synchronises the device first.  Reconstruction calls
+ * fail with PAT_ERR_INVALID until pat_bp_restore. */
+pat_status pat_bp_evict(pat_bp_t h);
+
+/* pat_bp_restore -- reallocate the device table and copy it back from the
+ * pinned host mirror, asynchronously on stream (no-op when resident). */
+pat_status pat_bp_restore(pat_bp_t h, pat_stream_t stream);
+
 /* pat_bp_destroy -- free the handle and its device memory (synchronises). */
 pat_status pat_bp_destroy(pat_bp_t h);
 
@@ -237,6 +248,64 @@ pat_status pat_bp_reconstruct_multi(const pat_bp_t* handles, const void* const* 
 pat_status pat_bp_autotune(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
                            const float* scales_dev, int n_frames, float* out_dev,
                            pat_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: frames arrive one request at a time for several registered
+ * subjects (speed maps); a scheduler thread keeps tables resident on the
+ * device within an HBM budget (least recently used tables are evicted to a
+ * pinned host copy and reloaded on demand), batches the pending frames of a
+ * subject into one reconstruction, and runs batches of different subjects
+ * concurrently on several streams while new requests keep arriving
+ * (continuous batching).  Every result is bit-identical to reconstructing
+ * that frame alone with pat_bp_reconstruct.
+ * ------------------------------------------------------------------------ */
+typedef struct pat_srv_s* pat_srv_t;
+
+typedef struct {
+  int n_streams;        /* batches in flight at once (default 4)                */
+  int max_batch_frames; /* frames of one subject in one batch (default 16)      */
+  int max_queue;        /* pending requests before submit says BUSY (def. 4096) */
+  int stall_us;         /* test hook: scheduler sleeps this long per cycle (0)  */
+} pat_srv_cfg;
+
+typedef struct {
+  uint64_t submitted, completed, failed;
+  uint64_t batches, uploads, evictions;
+  double p50_ms, p99_ms, mean_batch_frames;
+  size_t resident_bytes, budget_bytes;
+} pat_srv_stats_t;
+
+/* pat_srv_create -- hbm_budget: device bytes the resident tables and their
+ * working buffers may use; cfg may be NULL (defaults).  Starts the scheduler
+ * thread on the current device. */
+pat_status pat_srv_create(size_t hbm_budget, const pat_srv_cfg* cfg, pat_srv_t* out);
+
+/* pat_srv_register -- arguments of pat_bp_create; builds the subject's table
+ * (host fast marching) and keeps a pinned host copy for reloads.  The table
+ * is uploaded when a request needs it.  Blocking. */
+pat_status pat_srv_register(pat_srv_t srv, const float* speed_host, const pat_grid* grid,
+                            const double* sensors_host, int n_sensors, const uint8_t* mask_host,
+                            const float* weights_host, double dt, int n_samples, unsigned flags,
+                            int* subject_id);
+
+/* pat_srv_submit -- one frame: signals_host [N_s][N_t] of dtype (scales_host
+ * [N_s] for 16-bit dtypes), result written to out_host (dense grid or compact,
+ * as the subject's flags say).  Both host buffers must stay valid until
+ * pat_srv_poll reports the ticket done.  Errors: PAT_ERR_NOT_FOUND (unknown
+ * subject), PAT_ERR_BUSY (queue full), PAT_ERR_INVALID. */
+pat_status pat_srv_submit(pat_srv_t srv, int subject, const void* signals_host, pat_dtype dtype,
+                          const float* scales_host, float* out_host, uint64_t* ticket);
+
+/* pat_srv_poll -- wait up to timeout_us (0 = do not wait) for the ticket.
+ * Returns PAT_PENDING while in flight, else the request's final status (and
+ * forgets the ticket); latency_s (may be NULL) receives submit-to-done time.
+ * PAT_ERR_NOT_FOUND for an unknown or already reported ticket. */
+pat_status pat_srv_poll(pat_srv_t srv, uint64_t ticket, int timeout_us, double* latency_s);
+
+pat_status pat_srv_stats(pat_srv_t srv, pat_srv_stats_t* stats);
+
+/* pat_srv_destroy -- finish everything in flight, stop the scheduler, free. */
+pat_status pat_srv_destroy(pat_srv_t srv);
 
 /* pat_test_wait_timeout -- launches one CTA whose mbarrier wait can never
  * complete, bounded by timeout_ns; returns PAT_ERR_TIMEOUT when the kernel

@@ -20,7 +20,7 @@ import numpy as np
 from . import _lib
 from ._lib import PatError
 
-__all__ = ["BP", "Plan", "PatError", "fmm_host", "table_host", "reconstruct_multi",
+__all__ = ["BP", "Plan", "Server", "PatError", "fmm_host", "table_host", "reconstruct_multi",
            "wait_timeout_probe", "DTYPES"]
 
 DTYPES = {"f32": _lib.PAT_F32, "bf16": _lib.PAT_BF16, "f16": _lib.PAT_F16}
@@ -201,6 +201,13 @@ class BP:
             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "pat_bp_autotune")
         return out
 
+    def evict(self):
+        """Free the device table (needs flags |= PAT_FLAG_HOST_MIRROR at creation)."""
+        _lib.check(self._lib.pat_bp_evict(self._h), "pat_bp_evict")
+
+    def restore(self, stream=None):
+        _lib.check(self._lib.pat_bp_restore(self._h, _stream_ptr(stream)), "pat_bp_restore")
+
     def reserve(self, max_frames, dtype="f32"):
         _lib.check(self._lib.pat_bp_reserve(self._h, int(max_frames), DTYPES[dtype]),
                    "pat_bp_reserve")
@@ -280,6 +287,84 @@ class Plan:
         if getattr(self, "_h", None):
             self._lib.pat_plan_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop over several subjects (speed maps)
+    within an HBM budget.  submit() takes one frame [ns, nt] (float32, or
+    uint16 codes with float32 scales [ns] for 'bf16'/'f16') and a float32
+    output array; both are kept alive here until the ticket is polled done."""
+
+    def __init__(self, hbm_budget, n_streams=4, max_batch_frames=16, max_queue=4096, stall_us=0):
+        lib = _lib.load()
+        self._lib = lib
+        cfg = _lib.PatSrvCfg(n_streams, max_batch_frames, max_queue, stall_us)
+        h = ctypes.c_void_p()
+        _lib.check(lib.pat_srv_create(int(hbm_budget), ctypes.byref(cfg), ctypes.byref(h)),
+                   "pat_srv_create")
+        self._h = h
+        self._keep = {}
+        self.shapes = []
+
+    def register(self, speed, dx, origin, sensors, dt, n_samples, mask=None, weights=None,
+                 flags=0, compact=False):
+        speed = np.ascontiguousarray(speed, dtype=np.float32)
+        g = _lib.make_grid(speed.shape, dx, origin)
+        sensors = np.ascontiguousarray(sensors, dtype=np.float64)
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        if compact:
+            flags |= _lib.PAT_FLAG_COMPACT_OUT
+        sid = ctypes.c_int()
+        _lib.check(self._lib.pat_srv_register(
+            self._h, speed.ctypes.data, ctypes.byref(g), sensors.ctypes.data, sensors.shape[0],
+            None if m is None else m.ctypes.data, None if w is None else w.ctypes.data, float(dt),
+            int(n_samples), int(flags), ctypes.byref(sid)), "pat_srv_register")
+        npix = int(np.count_nonzero(m)) if m is not None else speed.size
+        self.shapes.append((npix,) if compact else tuple(speed.shape))
+        return sid.value
+
+    def submit(self, subject, signals, out, dtype="f32", scales=None):
+        sig = np.ascontiguousarray(signals)
+        sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+        if out.dtype != np.float32 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous float32 array")
+        t = ctypes.c_uint64()
+        _lib.check(self._lib.pat_srv_submit(self._h, int(subject), sig.ctypes.data, DTYPES[dtype],
+                                            None if sc is None else sc.ctypes.data,
+                                            out.ctypes.data, ctypes.byref(t)), "pat_srv_submit")
+        self._keep[t.value] = (sig, sc, out)
+        return t.value
+
+    def poll(self, ticket, timeout_us=0):
+        """(status, latency_s); status PAT_PENDING (7) while in flight."""
+        lat = ctypes.c_double()
+        st = self._lib.pat_srv_poll(self._h, int(ticket), int(timeout_us), ctypes.byref(lat))
+        if st != _lib.PAT_PENDING:
+            self._keep.pop(ticket, None)
+        return st, lat.value
+
+    def wait(self, ticket, timeout_s=30.0):
+        st, lat = self.poll(ticket, int(timeout_s * 1e6))
+        _lib.check(st, "pat_srv_poll")
+        return lat
+
+    def stats(self):
+        st = _lib.PatSrvStats()
+        _lib.check(self._lib.pat_srv_stats(self._h, ctypes.byref(st)), "pat_srv_stats")
+        return {k: getattr(st, k) for k, _ in _lib.PatSrvStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pat_srv_destroy(self._h)
+            self._h = None
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -28,7 +28,10 @@ EXPORTS = (
     "pat_bp_table", "pat_bp_destroy", "pat_fmm_host", "pat_table_host",
     "pat_test_wait_timeout", "pat_plan_create", "pat_plan_execute", "pat_plan_sync",
     "pat_plan_info", "pat_plan_destroy", "pat_bp_reconstruct_multi", "pat_bp_autotune",
+    "pat_bp_evict", "pat_bp_restore", "pat_srv_create", "pat_srv_register", "pat_srv_submit",
+    "pat_srv_poll", "pat_srv_stats", "pat_srv_destroy",
 )
+PAT_FLAG_HOST_MIRROR = 0x100
 PAT_PLAN_AUTOTUNE = 0x1
 PAT_PLAN_GRAPH = 0x2
 
@@ -53,6 +56,20 @@ class PatPlanInfo(ctypes.Structure):
                 ("smem_budget_kb", ctypes.c_int), ("grid", ctypes.c_int),
                 ("n_units", ctypes.c_int64), ("tuned", ctypes.c_int), ("graph", ctypes.c_int),
                 ("tune_ms", ctypes.c_double)]
+
+
+class PatSrvCfg(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int), ("max_batch_frames", ctypes.c_int),
+                ("max_queue", ctypes.c_int), ("stall_us", ctypes.c_int)]
+
+
+class PatSrvStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("uploads", ctypes.c_uint64), ("evictions", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_batch_frames", ctypes.c_double), ("resident_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t)]
 
 
 class PatError(RuntimeError):
@@ -126,6 +143,23 @@ def load():
         lib.pat_bp_reconstruct_multi.argtypes = [_pp, _pp, _i, _pp, ctypes.POINTER(_i), _pp, _i, _vp]
         lib.pat_bp_autotune.restype = _i
         lib.pat_bp_autotune.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp]
+        lib.pat_bp_evict.restype = _i
+        lib.pat_bp_evict.argtypes = [_vp]
+        lib.pat_bp_restore.restype = _i
+        lib.pat_bp_restore.argtypes = [_vp, _vp]
+        lib.pat_srv_create.restype = _i
+        lib.pat_srv_create.argtypes = [ctypes.c_size_t, ctypes.POINTER(PatSrvCfg), _pp]
+        lib.pat_srv_register.restype = _i
+        lib.pat_srv_register.argtypes = [_vp, _vp, ctypes.POINTER(PatGrid), _vp, _i, _vp, _vp, _d, _i,
+                                         _u, ctypes.POINTER(_i)]
+        lib.pat_srv_submit.restype = _i
+        lib.pat_srv_submit.argtypes = [_vp, _i, _vp, _i, _vp, _vp, ctypes.POINTER(_u64)]
+        lib.pat_srv_poll.restype = _i
+        lib.pat_srv_poll.argtypes = [_vp, _u64, _i, ctypes.POINTER(_d)]
+        lib.pat_srv_stats.restype = _i
+        lib.pat_srv_stats.argtypes = [_vp, ctypes.POINTER(PatSrvStats)]
+        lib.pat_srv_destroy.restype = _i
+        lib.pat_srv_destroy.argtypes = [_vp]
         lib.pat_test_wait_timeout.restype = _i
         lib.pat_test_wait_timeout.argtypes = [_u64]
         _lib = lib

@@ -72,6 +72,11 @@ struct pat_bp_s {
   size_t scales_cap = 0;
   float* d_out = nullptr;
   size_t out_cap = 0;
+  // pinned host copy of the device table (PAT_FLAG_HOST_MIRROR): u, base, slot,
+  // zero runs, weights; lets the device copy be dropped and reloaded
+  void* mirror[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t mirror_bytes[5] = {0, 0, 0, 0, 0};
+  bool evicted = false;
   std::mutex mu;
 };
 
@@ -91,6 +96,16 @@ GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst);
 PreParams make_pre(pat_bp_t h, const void* sig, pat_dtype dtype, const float* scales, int n_frames,
                    int FB);
 InstDesc make_desc(pat_bp_t h, float* out, int n_frames, int FB, int wst);
+// device bytes the handle holds now (table plus working buffers)
+size_t resident_bytes(pat_bp_t h);
+// device bytes of the table alone
+size_t table_device_bytes(pat_bp_t h);
+pat_status evict_locked(pat_bp_t h);
+// preprocess + gather on stream (caller holds h->mu or owns h exclusively)
+pat_status reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                              const float* scales_dev, int n_frames, float* out_dev,
+                              cudaStream_t stream);
+pat_status restore_locked(pat_bp_t h, cudaStream_t st);
 // resident gather CTAs for a config (cached per config)
 int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm);
 

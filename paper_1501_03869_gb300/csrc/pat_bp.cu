@@ -95,6 +95,7 @@ static void free_handle(pat_bp_t h) {
   cudaFree(h->d_sig);
   cudaFree(h->d_scales);
   cudaFree(h->d_out);
+  for (int i = 0; i < 5; ++i) cudaFreeHost(h->mirror[i]);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }
@@ -187,6 +188,21 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
       (st = upload(&h->d_w, w, "weights")) != PAT_OK) {
     free_handle(h);
     return st;
+  }
+  if (flags & PAT_FLAG_HOST_MIRROR) {
+    const void* src[5] = {tab.u.data(), packed.data(),
+                          (h->compact ? tab.slot_compact : tab.slot_dense).data(),
+                          tab.zero_runs.data(), w.data()};
+    const size_t bytes[5] = {tab.u.size() * 4, packed.size() * 4, tab.slot_dense.size() * 4,
+                             std::max<size_t>(tab.zero_runs.size(), 1) * 4, w.size() * 4};
+    for (int i = 0; i < 5; ++i) {
+      if (cudaMallocHost(&h->mirror[i], bytes[i]) != cudaSuccess) {
+        free_handle(h);
+        return fail(PAT_ERR_OOM, "pinned host mirror");
+      }
+      h->mirror_bytes[i] = bytes[i];
+      if (i != 3 || !tab.zero_runs.empty()) std::memcpy(h->mirror[i], src[i], bytes[i]);
+    }
   }
   if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess) {
     free_handle(h);
@@ -372,6 +388,72 @@ int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm) {
 
 }  // namespace patbp
 
+namespace patbp {
+
+size_t table_device_bytes(pat_bp_t h) {
+  return size_t(h->n_tiles) * h->ns * h->P * 4 + size_t(h->n_tiles) * h->ns_pad * 4 +
+         size_t(h->n_tiles) * h->P * 4 + std::max<size_t>(size_t(h->n_zero_runs) * 2, 1) * 4 +
+         size_t(h->ns) * 4;
+}
+
+size_t resident_bytes(pat_bp_t h) {
+  if (h->evicted) return 0;
+  return table_device_bytes(h) + h->b_cap + h->m_cap + h->part_cap + h->counter_cap;
+}
+
+pat_status evict_locked(pat_bp_t h) {
+  if (!h->mirror[0]) return fail(PAT_ERR_INVALID, "eviction needs PAT_FLAG_HOST_MIRROR");
+  if (h->evicted) return PAT_OK;
+  PAT_CUDA(cudaDeviceSynchronize());
+  void** dev[9] = {reinterpret_cast<void**>(&h->d_u), reinterpret_cast<void**>(&h->d_base),
+                   reinterpret_cast<void**>(&h->d_slot), reinterpret_cast<void**>(&h->d_zero_runs),
+                   reinterpret_cast<void**>(&h->d_w), &h->d_b, reinterpret_cast<void**>(&h->d_m),
+                   reinterpret_cast<void**>(&h->d_part), reinterpret_cast<void**>(&h->d_counter)};
+  for (void** p : dev) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  h->b_cap = h->m_cap = h->part_cap = h->counter_cap = 0;
+  h->pre_frames = 0;
+  h->evicted = true;
+  return PAT_OK;
+}
+
+pat_status restore_locked(pat_bp_t h, cudaStream_t st) {
+  if (!h->evicted) return PAT_OK;
+  void** dev[5] = {reinterpret_cast<void**>(&h->d_u), reinterpret_cast<void**>(&h->d_base),
+                   reinterpret_cast<void**>(&h->d_slot), reinterpret_cast<void**>(&h->d_zero_runs),
+                   reinterpret_cast<void**>(&h->d_w)};
+  for (int i = 0; i < 5; ++i) {
+    if (cudaMalloc(dev[i], h->mirror_bytes[i]) != cudaSuccess) {
+      for (int j = 0; j <= i; ++j) {
+        cudaFree(*dev[j]);
+        *dev[j] = nullptr;
+      }
+      return fail(PAT_ERR_OOM, "table restore");
+    }
+    PAT_CUDA(cudaMemcpyAsync(*dev[i], h->mirror[i], h->mirror_bytes[i], cudaMemcpyHostToDevice, st));
+  }
+  h->evicted = false;
+  return PAT_OK;
+}
+
+}  // namespace patbp
+
+extern "C" pat_status pat_bp_evict(pat_bp_t h) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  PAT_CUDA(cudaSetDevice(h->device));
+  return evict_locked(h);
+}
+
+extern "C" pat_status pat_bp_restore(pat_bp_t h, pat_stream_t stream) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  PAT_CUDA(cudaSetDevice(h->device));
+  return restore_locked(h, static_cast<cudaStream_t>(stream));
+}
+
 static pat_status ensure_buffers(pat_bp_t h, int n_frames) {
   return ensure_buffers_fb(h, n_frames, frames_per_group(n_frames));
 }
@@ -386,6 +468,7 @@ extern "C" pat_status pat_bp_reserve(pat_bp_t h, int max_frames, pat_dtype dtype
 
 static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
                                     const float* scales_dev, int n_frames, cudaStream_t stream) {
+  if (h->evicted) return fail(PAT_ERR_INVALID, "the handle's table is evicted (pat_bp_restore)");
   if (!signals_dev) return fail(PAT_ERR_INVALID, "signals NULL");
   if (n_frames < 1 || n_frames > 65535) return fail(PAT_ERR_INVALID, "n_frames must be 1..65535");
   if (dtype != PAT_F32 && dtype != PAT_BF16 && dtype != PAT_F16)
@@ -431,9 +514,9 @@ static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaSt
   return PAT_OK;
 }
 
-static pat_status reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
-                                     const float* scales_dev, int n_frames, float* out_dev,
-                                     cudaStream_t stream) {
+pat_status patbp::reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                                      const float* scales_dev, int n_frames, float* out_dev,
+                                      cudaStream_t stream) {
   if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
   pat_status st = preprocess_locked(h, signals_dev, dtype, scales_dev, n_frames, stream);
   if (st != PAT_OK) return st;

@@ -147,6 +147,7 @@ namespace {
 pat_status refresh_buffers(pat_plan_t pl) {
   for (size_t i = 0; i < pl->hs.size(); ++i) {
     pat_bp_t h = pl->hs[i];
+    if (h->evicted) return fail(PAT_ERR_INVALID, "a plan handle's table is evicted");
     pat_status st = ensure_buffers_fb(h, pl->frames[i], pl->FB);
     if (st != PAT_OK) return st;
     pl->pre->inst[i].b = h->d_b;
