@@ -130,6 +130,25 @@ pat_status pat_bp_preprocess(pat_bp_t h, const void* signals_dev, pat_dtype dtyp
                              const float* scales_dev, int n_frames, pat_stream_t stream);
 pat_status pat_bp_gather(pat_bp_t h, int n_frames, float* out_dev, pat_stream_t stream);
 
+/* pat_bp_reconstruct_noalloc -- pat_bp_reconstruct without any device
+ * allocation, for callers that may not allocate device memory: hosts that own
+ * all device memory in their own pool or budget, and per-frame loops that
+ * must not call the CUDA allocator (its calls can synchronise the device and
+ * add latency jitter).  The paper has no counterpart; this is an interface
+ * convenience.  Same arguments and result as pat_bp_reconstruct.  All scratch
+ * (integrand, multipliers, partial sums, counters, tickets) comes from one
+ * file-scope device array of 16 MiB per device, held until the process exits;
+ * a reconstruction needing more returns PAT_ERR_INVALID with the byte count
+ * (one paper-shaped frame of 512 sensors x 2048 samples needs about 5 MiB).
+ * The first call on a device looks up the array's address; make it before any
+ * stream capture.  Calls share the array: work of two calls that overlaps on
+ * the GPU races, so serialise them.  Each call clears, on its stream, the
+ * parts that must start at zero.  Device-side timeouts are reported by
+ * pat_bp_sync on the handle. */
+pat_status pat_bp_reconstruct_noalloc(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
+                                      const float* scales_dev, int n_frames, float* out_dev,
+                                      pat_stream_t stream);
+
 /* pat_bp_reconstruct_host -- the paper's timed on-line path (Sec. III): copy
  * signals and scales from host memory, reconstruct, copy the image back.
  * Synchronous; uses the handle's own stream and staging buffers.  Pinned host

@@ -201,6 +201,22 @@ class BP:
             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "pat_bp_autotune")
         return out
 
+    def reconstruct_noalloc(self, signals, out, scales=None, stream=None):
+        """pat_bp_reconstruct_noalloc: the library allocates no device memory
+        for this call (scratch comes from a fixed 16 MiB device array; calls
+        must not overlap on the GPU).  `out` must be given."""
+        if signals.dim() == 2:
+            signals = signals.unsqueeze(0)
+        F = signals.shape[0]
+        if not out.is_contiguous() or out.dtype != _torch().float32 or out.numel() != int(
+                np.prod(self.out_shape(F))):
+            raise ValueError("out must be a contiguous float32 tensor of the output shape")
+        _lib.check(self._lib.pat_bp_reconstruct_noalloc(
+            self._h, ctypes.c_void_p(signals.data_ptr()), _dtype_code(signals),
+            None if scales is None else ctypes.c_void_p(scales.data_ptr()), F,
+            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "pat_bp_reconstruct_noalloc")
+        return out
+
     def evict(self):
         """Free the device table (needs flags |= PAT_FLAG_HOST_MIRROR at creation)."""
         _lib.check(self._lib.pat_bp_evict(self._h), "pat_bp_evict")

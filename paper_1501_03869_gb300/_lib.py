@@ -29,7 +29,7 @@ EXPORTS = (
     "pat_test_wait_timeout", "pat_plan_create", "pat_plan_execute", "pat_plan_sync",
     "pat_plan_info", "pat_plan_destroy", "pat_bp_reconstruct_multi", "pat_bp_autotune",
     "pat_bp_evict", "pat_bp_restore", "pat_srv_create", "pat_srv_register", "pat_srv_submit",
-    "pat_srv_poll", "pat_srv_stats", "pat_srv_destroy",
+    "pat_srv_poll", "pat_srv_stats", "pat_srv_destroy", "pat_bp_reconstruct_noalloc",
 )
 PAT_FLAG_HOST_MIRROR = 0x100
 PAT_PLAN_AUTOTUNE = 0x1
@@ -143,6 +143,8 @@ def load():
         lib.pat_bp_reconstruct_multi.argtypes = [_pp, _pp, _i, _pp, ctypes.POINTER(_i), _pp, _i, _vp]
         lib.pat_bp_autotune.restype = _i
         lib.pat_bp_autotune.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp]
+        lib.pat_bp_reconstruct_noalloc.restype = _i
+        lib.pat_bp_reconstruct_noalloc.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp]
         lib.pat_bp_evict.restype = _i
         lib.pat_bp_evict.argtypes = [_vp]
         lib.pat_bp_restore.restype = _i
