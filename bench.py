@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-multi", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=300)
     return ap.parse_args()
 
 
@@ -194,6 +197,84 @@ def run_reference(args, rank, world):
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def multi_form(args, flush, stream):
+    """Uneven instances in one persistent launch: the 32-instance workload
+    (grids 96^2-384^2, 128-1024 sensors, 1024-4096 samples, 1-16 frames),
+    autotuned, replayed as a CUDA graph; L2 flushed before every execution."""
+    import torch
+    from paper_1501_03869_gb300 import BP, Plan, synth
+    ws = [synth.config4_instance(i) for i in range(32)]
+    bps = [BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask) for w in ws]
+    sig = [torch.from_numpy(w.signals).cuda() for w in ws]
+    outs = [torch.empty(bp.out_shape(w.n_frames), device="cuda") for bp, w in zip(bps, ws)]
+    plan = Plan(bps, [w.n_frames for w in ws], autotune=True, graph=True)
+    plan.execute(sig, outs)
+    plan.sync()
+    Ev = torch.cuda.Event
+    recs = []
+    for i in range(max(5, min(args.steps // 100, 40)) + 3):
+        flush.zero_()
+        e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
+        e0.record(stream)
+        plan.execute(sig, outs, stream=stream)
+        e1.record(stream)
+        recs.append((e0, e1))
+    plan.sync(stream)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in recs[3:])
+    frames = sum(w.n_frames for w in ws)
+    upd = sum(w.n_frames * w.n_sensors * w.n_pix for w in ws)
+    info = plan.info
+    plan.close()
+    for bp in bps:
+        bp.close()
+    return {"workload": "32 uneven instances, one persistent launch, CUDA graph", "frames": frames,
+            "ms_per_execution": ms, "frames_per_s": frames / (ms / 1e3),
+            "value": upd / (ms / 1e3) / 1e9, "unit": UNIT, "launch_shape": info,
+            "gpu_launches_per_execution": 2}
+
+
+def serving_form(args):
+    """Request loop over several 3-D subjects (hemisphere of sensors around a
+    spherical-shell skull, BF16 signals of 2048 samples): Poisson arrivals at
+    several rates, frames/s and p50/p99 submit-to-done latency."""
+    import torch  # noqa: F401  (CUDA context)
+    from paper_1501_03869_gb300 import Server, synth
+    shape, n_s, n_sub = (48, 80, 80), 256, 4
+    subs = [synth.config5_subject(k, n_frames=4, n_sensors=n_s, shape=shape, dx=0.5e-3)
+            for k in range(n_sub)]
+    srv = Server(hbm_budget=120 << 30, n_streams=4, max_batch_frames=16)
+    ids = [srv.register(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask) for w in subs]
+    q = [synth.quantise(w.signals, "bf16") for w in subs]
+    rng = np.random.default_rng(5)
+    out = {"workload": f"{n_sub} 3-D subjects {shape[::-1]} at 0.5 mm, {n_s} sensors on a hemisphere, "
+                       "BF16 signals of 2048 samples, HBM budget 120 GB", "rates": []}
+    for rate in (200.0, 800.0, 3200.0):
+        n = args.serving_requests
+        gaps = rng.exponential(1.0 / rate, n)
+        pending = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(n):
+            t_next += gaps[i]
+            while time.perf_counter() < t_next:
+                pass
+            k = int(rng.integers(n_sub))
+            f = int(rng.integers(subs[k].n_frames))
+            codes, sc, _ = q[k]
+            o = np.empty(subs[k].speed.shape, np.float32)
+            pending.append(srv.submit(ids[k], codes[f], o, dtype="bf16", scales=sc[f]))
+        lat = [srv.wait(t) for t in pending]
+        el = time.perf_counter() - t0
+        out["rates"].append({"offered_fps": rate, "requests": n, "frames_per_s": n / el,
+                             "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                             "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+    st = srv.stats()
+    out["mean_batch_frames"] = st["mean_batch_frames"]
+    out["batches"] = st["batches"]
+    srv.close()
+    return out
 
 
 def time_steps(fn, steps, warmup, stream, flush):
@@ -358,6 +439,11 @@ def main():
             forms[name] = {"frames": F, "ms_per_batch": ms, "frames_per_s": F / (ms / 1e3),
                            "value": F * updates / (ms / 1e3) / 1e9, "unit": UNIT}
         bp.sync()
+
+    if not args.no_multi and world == 1:
+        forms["multi_instance_c4"] = multi_form(args, flush, stream)
+    if not args.no_serving and world == 1:
+        forms["serving_3d"] = serving_form(args)
 
     # -------------------------------------------------------- cpu baseline --
     cpu = None

@@ -294,16 +294,20 @@ pat_status autotune(pat_plan_t pl, const void* const* sig, const float* const* s
         }
         fill_pointers(pl, sig, scales, outs);
         if (launch_both(pl, st) != PAT_OK) continue;  // warm-up
-        cudaEventRecord(e0, st);
-        if (launch_both(pl, st) != PAT_OK) continue;
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return cuda_fail(cudaGetLastError(), "autotune run");
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {  // best of three
+          cudaEventRecord(e0, st);
+          if (launch_both(pl, st) != PAT_OK) break;
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(cudaGetLastError(), "autotune run");
+          }
+          float t = 0.0f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms = std::min(ms, t);
         }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
           best = ms;
           bfb = fb;
