@@ -318,6 +318,7 @@ def main():
     out = torch.empty(bp.out_shape(1), device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     bp.reserve(max(args.batch_frames, 1))
+    bp.autotune(sig, out=out)  # the project's autotuner picks the launch shape
     Ev = torch.cuda.Event
 
     def step_kernels():
@@ -419,26 +420,31 @@ def main():
     forms = {}
     if not args.no_forms and args.batch_frames > 1:
         F = args.batch_frames
+        from paper_1501_03869_gb300 import _lib
+        bpb = BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+                 flags=_lib.PAT_FLAG_TILE_256)
         rng = np.random.default_rng(7)
         sigF = torch.from_numpy(
             (w.signals[0][None] * rng.uniform(0.5, 1.5, (F, 1, 1))).astype(np.float32)).to(dev)
-        outF = torch.empty(bp.out_shape(F), device=dev)
+        outF = torch.empty(bpb.out_shape(F), device=dev)
         codes, sc, _ = synth.quantise(sigF.cpu().numpy(), "bf16")
         sig16 = torch.from_numpy(codes.astype(np.int16)).to(dev).view(torch.bfloat16)
         sc16 = torch.from_numpy(sc).to(dev)
         for name, s, scl in (("batched_f32", sigF, None), ("batched_bf16", sig16, sc16)):
+            bpb.autotune(s, scales=scl, out=outF)
             def fstep(s=s, scl=scl):
                 e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
                 e0.record(stream)
-                bp.reconstruct(s, scales=scl, out=outF, stream=stream)
+                bpb.reconstruct(s, scales=scl, out=outF, stream=stream)
                 e1.record(stream)
                 return e0, e1
             n_rep = max(3, args.steps // 5)
             rr = time_steps(fstep, n_rep, 2, stream, flush)
             ms = statistics.mean(a.elapsed_time(b) for a, b in rr)
             forms[name] = {"frames": F, "ms_per_batch": ms, "frames_per_s": F / (ms / 1e3),
-                           "value": F * updates / (ms / 1e3) / 1e9, "unit": UNIT}
-        bp.sync()
+                           "value": F * updates / (ms / 1e3) / 1e9, "unit": UNIT, "tile_pix": 256}
+        bpb.sync()
+        bpb.close()
 
     if not args.no_multi and world == 1:
         forms["multi_instance_c4"] = multi_form(args, flush, stream)

@@ -99,6 +99,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+__device__ __forceinline__ int atomic_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void named_barrier(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
@@ -479,13 +485,70 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
       abort_now();
       return false;
     };
-    int64_t t_cur = 0, t_next = 0;
-    if (lane == 0) {
-      t_cur = atomicAdd(reinterpret_cast<unsigned long long*>(p.sched), 1ull);
-      t_next = t_cur < N ? int64_t(atomicAdd(reinterpret_cast<unsigned long long*>(p.sched), 1ull)) : N;
-    }
-    t_cur = __shfl_sync(0xffffffffu, t_cur, 0);
+    // Issue stage st for sensors [s0, s0 + S) of unit q: the table block (part
+    // & 1) and/or the multipliers and windows (part & 2), which come from the
+    // preprocessing grid.  The stage's expected bytes are posted with the
+    // table block (or with everything when part == 3).
+    auto issue_chunk = [&](const UnitPos& q, const InstDesc& d, const int* mrow, int s0, int st,
+                           int part) {
+      const int se = min(p.S, q.s_hi - s0);
+      const int se4 = (se + 3) & ~3;
+      unsigned char* sb = stage0 + st * L.bytes;
+      int bs = 0, wl = 0;
+      if (lane < se) {
+        const uint32_t word = uint32_t(mrow[s0 - q.s_lo + lane]);
+        bs = int(word & 0xffffu);
+        wl = int(word >> 16);
+      }
+      int incl = wl;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int total_w = __shfl_sync(0xffffffffu, incl, 31);
+      int off = incl - wl;
+      uint32_t wrows = uint32_t(total_w);
+      if (total_w > p.Wst) {  // cannot happen with a host-computed Wst; stay in bounds
+        if (lane == 0 && (part & 1)) atomicOr(p.status, kStatusBadConfig);
+        wl = 0;
+        off = 0;
+        wrows = 0;
+      }
+      if (part & 1) {
+        if (lane < S4) reinterpret_cast<int*>(sb + L.off)[lane] = lane < se ? off : 0;
+        __syncwarp();
+        const uint32_t bytes = uint32_t(se) * P * 4 + uint32_t(se4) * FB * 4 + wrows * FB * 4;
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&full[st], bytes);
+          bulk_g2s(sb + L.u, d.u + (int64_t(q.tile) * d.n_sensors + s0) * P, uint32_t(se) * P * 4,
+                   &full[st]);
+        }
+      }
+      if (part & 2) {
+        if (lane == 0)
+          bulk_g2s(sb + L.m, d.m + (int64_t(q.fg) * d.n_sensors_pad + s0) * FB,
+                   uint32_t(se4) * FB * 4, &full[st]);
+        if (wl > 0) {
+          const unsigned char* src =
+              static_cast<const unsigned char*>(d.b) +
+              ((int64_t(q.fg) * d.n_sensors + s0 + lane) * d.n_t_pad + bs) * (FB * 4);
+          bulk_g2s(sb + L.win + size_t(off) * FB * 4, src, uint32_t(wl) * FB * 4, &full[st]);
+        }
+      }
+    };
+    // the first unit of every CTA is blockIdx.x (no ticket round trip at the
+    // start); later units come from the ticket, offset by the grid size
+    auto next_ticket = [&]() -> int64_t {
+      int64_t t = N;
+      if (lane == 0)
+        t = int64_t(gridDim.x) + int64_t(atomicAdd(reinterpret_cast<unsigned long long*>(p.sched), 1ull));
+      return t;
+    };
+    int64_t t_cur = int64_t(blockIdx.x) < N ? int64_t(blockIdx.x) : N;
+    int64_t t_next = t_cur < N ? next_ticket() : N;
     t_next = __shfl_sync(0xffffffffu, t_next, 0);
+    if (t_next > N) t_next = N;
     if (t_cur < N) issue_meta(t_cur, 0);
     int64_t meta_last = t_cur < N ? 0 : -1;  // unit counter j of the last base copy requested
     bool ok = true;
@@ -504,64 +567,34 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
       if (t_next < N) {
         issue_meta(t_next, slot ^ 1);
         meta_last = j + 1;
-        if (lane == 0) t_next2 = int64_t(atomicAdd(reinterpret_cast<unsigned long long*>(p.sched), 1ull));
+        t_next2 = next_ticket();
       }
       if (lane == 0) unit_ring[j % kRing] = t_cur;
+      const int* mrow = meta + slot * kMaxG;
+      int s0 = q.s_lo;
       if (!waited_inputs) {
-        // the integrand and multipliers come from the preprocessing grid
+        // table blocks of the first stages stream while the preprocessing grid
+        // still runs; its outputs (multipliers, windows) only after the wait
+        const int64_t seq0 = seq;
+        int k = 0;
+        for (int s = q.s_lo; s < q.s_hi && k < p.stages; s += p.S, ++k)
+          issue_chunk(q, d, mrow, s, int((seq0 + k) % p.stages), 1);
         asm volatile("griddepcontrol.wait;" ::: "memory");
         waited_inputs = true;
+        for (int i = 0; i < k; ++i, s0 += p.S, ++seq)
+          issue_chunk(q, d, mrow, s0, int(seq % p.stages), 2);
       }
-      const int* mrow = meta + slot * kMaxG;
-      for (int s0 = q.s_lo; s0 < q.s_hi; s0 += p.S, ++seq) {
+      for (; s0 < q.s_hi; s0 += p.S, ++seq) {
         const int st = int(seq % p.stages);
         if (!acquire_stage(st)) {
           ok = false;
           break;
         }
-        const int se = min(p.S, q.s_hi - s0);
-        const int se4 = (se + 3) & ~3;
-        unsigned char* sb = stage0 + st * L.bytes;
-        int bs = 0, wl = 0;
-        if (lane < se) {
-          const uint32_t word = uint32_t(mrow[s0 - q.s_lo + lane]);
-          bs = int(word & 0xffffu);
-          wl = int(word >> 16);
-        }
-        int incl = wl;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const int total_w = __shfl_sync(0xffffffffu, incl, 31);
-        int off = incl - wl;
-        uint32_t wrows = uint32_t(total_w);
-        if (total_w > p.Wst) {  // cannot happen with a host-computed Wst; stay in bounds
-          if (lane == 0) atomicOr(p.status, kStatusBadConfig);
-          wl = 0;
-          off = 0;
-          wrows = 0;
-        }
-        if (lane < S4) reinterpret_cast<int*>(sb + L.off)[lane] = lane < se ? off : 0;
-        __syncwarp();
-        const uint32_t bytes = uint32_t(se) * P * 4 + uint32_t(se4) * FB * 4 + wrows * FB * 4;
-        if (lane == 0) {
-          mbar_arrive_expect_tx(&full[st], bytes);
-          bulk_g2s(sb + L.u, d.u + (int64_t(q.tile) * d.n_sensors + s0) * P, uint32_t(se) * P * 4,
-                   &full[st]);
-          bulk_g2s(sb + L.m, d.m + (int64_t(q.fg) * d.n_sensors_pad + s0) * FB,
-                   uint32_t(se4) * FB * 4, &full[st]);
-        }
-        if (wl > 0) {
-          const unsigned char* src =
-              static_cast<const unsigned char*>(d.b) +
-              ((int64_t(q.fg) * d.n_sensors + s0 + lane) * d.n_t_pad + bs) * (FB * 4);
-          bulk_g2s(sb + L.win + size_t(off) * FB * 4, src, uint32_t(wl) * FB * 4, &full[st]);
-        }
+        issue_chunk(q, d, mrow, s0, st, 3);
       }
       t_cur = t_next;
       t_next = __shfl_sync(0xffffffffu, t_next2, 0);
+      if (t_next > N) t_next = N;
     }
     // end of work: an empty stage whose unit index is -1
     if (ok) {
@@ -696,14 +729,14 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3))
       for (int fb = 0; fb < FB; ++fb)
 #pragma unroll
         for (int k = 0; k < KO; ++k) __stcg(mine + fb * P + k * 32 + lane, v[fb][k]);
-      // the last segment of a tile to finish sums all segments in fixed order
-      __threadfence();
+      // the last segment of a tile to finish sums all segments in fixed order;
+      // the counter's release/acquire orders the partials of every lane (the
+      // warp barrier before it makes the other lanes' stores part of the release)
       __syncwarp();
       int last = 0;
-      if (lane == 0) last = atomicAdd(d.counter + int64_t(q.fg) * d.n_tiles + q.tile, 1) == d.n_seg - 1;
+      if (lane == 0) last = atomic_add_acq_rel(d.counter + int64_t(q.fg) * d.n_tiles + q.tile, 1) == d.n_seg - 1;
       last = __shfl_sync(0xffffffffu, last, 0);
       if (!last) continue;
-      __threadfence();
 #pragma unroll
       for (int fb = 0; fb < FB; ++fb) {
         if (fb >= fb_eff) break;

@@ -303,7 +303,7 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
 
 // Launch shape for a frame count: the autotuned one when the handle has it,
 // else frames per unit by count, 16 (1 frame) or 8 sensors per stage and a
-// budget of four (1 frame) or two CTAs per SM.  When the stage windows are too
+// shared-memory budget of three (1 frame) or two CTAs per SM.  When the stage windows are too
 // long for that budget, the budget grows to the device limit and then fewer
 // frames share a unit.  No choice here changes the summation order.
 GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst) {
@@ -314,7 +314,7 @@ GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst) {
     if (h->tuned_S[fi][fmt] > 0)
       c = config_for(h, FB, h->tuned_S[fi][fmt], size_t(h->tuned_budget_kb[fi][fmt]) * 1024, wst);
     else
-      c = config_for(h, FB, FB == 1 ? 16 : 8, FB == 1 ? 55 * 1024 : 100 * 1024, wst);
+      c = config_for(h, FB, FB == 1 ? 16 : 8, FB == 1 ? 72 * 1024 : 100 * 1024, wst);
     if (gather_smem_bytes(c, *wst) <= limit) return c;
     c = config_for(h, FB, 8, limit, wst);
     if (gather_smem_bytes(c, *wst) <= limit) return c;
