@@ -233,3 +233,19 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     w = synth.config1(n_frames=1)
     got, _ = gpu_images(w)
     assert np.isfinite(got).all()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_config5_full_grid_sensor_subset(dtype):
+    """The serving volume at full size (160x160x96 voxels at 0.25 mm, all voxels
+    reconstructed) with a 16-sensor sub-handle of the 1024-sensor hemisphere:
+    every voxel against the oracle."""
+    w = synth.config5_subject(3, n_frames=1, n_sensors=1024)
+    sub = np.arange(0, 1024, 64)
+    ref = oracle_images(w, "c5_full_sub16", sensors_idx=sub)
+    got, info = gpu_images(w, sensors_idx=sub, dtype=dtype)
+    assert info["n_pix"] == 160 * 160 * 96
+    if dtype == "f32":
+        assert_fp32_parity(got, ref, np.abs(w.p0).max())
+    else:
+        assert rel_l2(got[0], ref[0]) <= LOWP_REL_L2
