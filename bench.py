@@ -11,7 +11,9 @@ Output: one JSON line (rank 0).  `value` is pixel*sensor updates per second
 (G/s) of the single-frame FP32 path with inputs resident in HBM, L2 flushed
 before every step; `e2e` is the same metric through pat_bp_reconstruct_host
 (pinned host buffers, copies inside the timed region); `forms` adds the
-batched FP32 / BF16 forms; `cpu_baseline` is the FP64 oracle on this host.
+batched FP32 / BF16 forms, the constant-speed (conventional) back projection
+of the same frame, many instances in one launch and 3-D serving;
+`cpu_baseline` is the FP64 oracle on this host.
 """
 from __future__ import annotations
 
@@ -34,6 +36,7 @@ UNIT = "G pixel*sensor updates/s"
 WORKLOAD = ("paper-shaped frame: 2D 256x256 dx 0.1 mm, skull ring 2200-3000 m/s, 512 sensors "
             "on a ring, 2048 FP32 samples, 21323-pixel disc mask, plain FP32 kernel")
 L2_FLUSH_BYTES = 512 << 20
+C_CONSTANT_BP = 1560.0  # m/s: the conventional back projection's speed in Sec. III
 
 
 def parse():
@@ -48,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-constant", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=300)
     return ap.parse_args()
 
@@ -277,6 +281,78 @@ def serving_form(args):
     return out
 
 
+def constant_form(args, w, flush, stream):
+    """The conventional back projection of the same frame (Sec. III's
+    comparison method, 1560 m/s): delays computed in the gather kernel, no
+    table stream.  Single frame as a replayed CUDA graph, and 64 frames."""
+    import torch
+    from paper_1501_03869_gb300 import BP
+    Ev = torch.cuda.Event
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bpc = BP.constant(C_CONSTANT_BP, w.speed.shape, w.dx, w.origin, w.sensors, w.dt, w.nt,
+                      mask=w.mask)
+    updates = bpc.info["n_pix"] * w.n_sensors
+    sig = torch.from_numpy(w.signals).to(dev)
+    out = torch.empty(bpc.out_shape(1), device=dev)
+    bpc.reserve(64)
+    bpc.autotune(sig, out=out)
+
+    def kern():
+        e0, e1, e2 = Ev(enable_timing=True), Ev(enable_timing=True), Ev(enable_timing=True)
+        e0.record(stream)
+        bpc.preprocess(sig, stream=stream)
+        e1.record(stream)
+        bpc.gather(1, out, stream=stream)
+        e2.record(stream)
+        return e0, e1, e2
+
+    kr = time_steps(kern, max(20, min(args.steps, 200)), args.warmup, stream, flush)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        bpc.reconstruct(sig, out=out, stream=side)
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bpc.reconstruct(sig, out=out, stream=torch.cuda.current_stream())
+
+    def step():
+        e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        return e0, e1
+
+    rr = time_steps(step, max(50, min(args.steps, 1000)), args.warmup, stream, flush)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in rr)
+    form = {"c0": C_CONSTANT_BP, "ms_per_step": ms, "frames_per_s": 1e3 / ms,
+            "value": updates / (ms / 1e3) / 1e9, "unit": UNIT,
+            "gather_us": statistics.mean(b.elapsed_time(c) for a, b, c in kr) * 1e3,
+            "preprocess_us": statistics.mean(a.elapsed_time(b) for a, b, c in kr) * 1e3,
+            "delay_bytes": bpc.info["table_bytes"]}
+    F = 64
+    rng = np.random.default_rng(9)
+    sigF = torch.from_numpy(
+        (w.signals[0][None] * rng.uniform(0.5, 1.5, (F, 1, 1))).astype(np.float32)).to(dev)
+    outF = torch.empty(bpc.out_shape(F), device=dev)
+    bpc.autotune(sigF, out=outF)
+
+    def fstep():
+        e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
+        e0.record(stream)
+        bpc.reconstruct(sigF, out=outF, stream=stream)
+        e1.record(stream)
+        return e0, e1
+
+    rr = time_steps(fstep, max(3, args.steps // 5), 2, stream, flush)
+    msF = statistics.mean(a.elapsed_time(b) for a, b in rr)
+    form["batched_f32"] = {"frames": F, "ms_per_batch": msF, "frames_per_s": F / (msF / 1e3),
+                           "value": F * updates / (msF / 1e3) / 1e9, "unit": UNIT}
+    bpc.sync()
+    bpc.close()
+    return form
+
+
 def time_steps(fn, steps, warmup, stream, flush):
     """Per-step device times (ms) of fn(); L2 flushed before every step, events
     on `stream`.  fn returns a list of (name, start_evt, end_evt) spans."""
@@ -446,6 +522,8 @@ def main():
         bpb.sync()
         bpb.close()
 
+    if not args.no_constant:
+        forms["constant_speed_c2"] = constant_form(args, w, flush, stream)
     if not args.no_multi and world == 1:
         forms["multi_instance_c4"] = multi_form(args, flush, stream)
     if not args.no_serving and world == 1:

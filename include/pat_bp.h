@@ -74,8 +74,11 @@ typedef struct {
   int window;           /* W: samples of one sensor a tile can touch          */
   int split;            /* sensor segments per tile (64 sensors each)         */
   int sensor_warps;     /* warps that share a tile's sensors inside one CTA   */
-  int64_t table_bytes;  /* device bytes of the travel-time table              */
-  double build_seconds; /* host time of the fast-marching table build         */
+  int64_t table_bytes;  /* device bytes of the delay data: the travel-time
+                           table, or the anchors and pixel terms (constant c)  */
+  double build_seconds; /* host time of the table (or anchor) build           */
+  int delays;           /* 0 fast-marching table, 1 constant speed            */
+  double c0;            /* the constant speed (m/s) when delays == 1, else 0  */
 } pat_bp_info_t;
 
 const char* pat_status_str(pat_status s);
@@ -92,7 +95,7 @@ const char* pat_last_error(void);
  *   sensors_host  [n_sensors][3] positions (m); each inside the grid box
  *   mask_host     [grid] nonzero = reconstruct that pixel; NULL = all nodes
  *   weights_host  [n_sensors] w_s of Eq. (BP); NULL = 1/n_sensors each
- *   dt, n_samples sample interval (s, > 0) and samples per signal (2..65536)
+ *   dt, n_samples sample interval (s, > 0) and samples per signal (2..32768)
  *   flags         PAT_FLAG_* (0 = defaults)
  *   out           receives the handle (owns all device memory it allocates)
  * Uses the current CUDA device.  Blocking.  Errors: PAT_ERR_INVALID for bad
@@ -101,6 +104,26 @@ pat_status pat_bp_create(const float* speed_host, const pat_grid* grid,
                          const double* sensors_host, int n_sensors,
                          const uint8_t* mask_host, const float* weights_host,
                          double dt, int n_samples, unsigned flags, pat_bp_t* out);
+
+/* pat_bp_create_constant -- the conventional back projection that Sec. III
+ * compares against: Eq. (BP) with the time of flight computed analytically
+ * for a constant sound speed (Sec. II-C), t_sj = |r_j - r_s| / c0 (Sec. III
+ * uses c0 = 1560 m/s).  No travel-time table is built or stored: the gather
+ * kernel evaluates every delay from a 32-byte anchor per (pixel tile, sensor)
+ * and 16 bytes per pixel (FP32, a few 1e-6 samples from the exact delay).
+ *   c0            sound speed (m/s), finite and > 0
+ *   sensors_host  [n_sensors][3] positions (m), anywhere (inside the grid box
+ *                 or not); for a 2-D grid only x and y are used
+ *   other arguments as pat_bp_create (the grid gives the pixel positions and
+ *                 the output geometry)
+ * Every other call (reconstruct, preprocess/gather, host round trip, plans,
+ * autotuning, eviction) accepts the handle; pat_bp_table returns its bases and
+ * slots but no offsets, and a plan takes only handles of one delay source.
+ * Blocking.  Errors: PAT_ERR_INVALID, PAT_ERR_OOM, PAT_ERR_CUDA. */
+pat_status pat_bp_create_constant(double c0, const pat_grid* grid, const double* sensors_host,
+                                  int n_sensors, const uint8_t* mask_host,
+                                  const float* weights_host, double dt, int n_samples,
+                                  unsigned flags, pat_bp_t* out);
 
 /* pat_bp_reconstruct -- the on-line step: Eq. (BP) for n_frames frames that
  * share the handle's table.
@@ -170,7 +193,9 @@ pat_status pat_bp_info(pat_bp_t h, pat_bp_info_t* info);
 /* pat_bp_table -- copy the device table back (tests): u_host [n_tiles][n_sensors]
  * [tile_pix] FP32 offsets, base_host [n_tiles][n_sensors] int32 bases, pix_host
  * [n_tiles * tile_pix] output index of each slot (-1 = padding).  Any pointer
- * may be NULL.  u + base is T/dt; entries out of the record hold 1e30. */
+ * may be NULL.  u + base is T/dt; entries out of the record hold 1e30.  A
+ * constant-speed handle has no offsets: u_host must be NULL for it
+ * (PAT_ERR_INVALID otherwise). */
 pat_status pat_bp_table(pat_bp_t h, float* u_host, int32_t* base_host, int32_t* pix_host);
 
 /* pat_bp_evict -- free the handle's device table and working buffers (needs

@@ -13,6 +13,9 @@ only compiles it with gcc on first use and marshals numpy arrays:
 * :func:`travel_table` -- one fast-marching run per sensor (Sec. II-B: each
   sensor is used as the source since ray paths are reversible), values read
   at the requested pixels.
+* :func:`constant_table` -- the conventional back projection's time of flight
+  for a constant sound speed (Sec. II-C; Sec. III compares at 1560 m/s):
+  straight-line distance over c0.
 * :func:`preprocess` -- Sec. II-C, Eq. (BP) integrand b = 2p - 2t dp/dt.
 * :func:`sample` / :func:`bp` -- Sec. II-C, Eq. (BP), P_j = sum_s w_s b_s(T_sj/dt)
   with linear interpolation, zero after the last sample.
@@ -130,6 +133,29 @@ def travel_table(speed, h, origin, sensors, pix):
     out = np.empty((sensors.shape[0], pix.size), dtype=np.float64)
     for s in range(sensors.shape[0]):
         out[s] = fmm_point(speed, h, origin, sensors[s]).ravel()[pix]
+    return out
+
+
+def node_positions(shape, h, origin, pix):
+    """[len(pix), 3] positions (m) of the nodes with linear indices pix (x
+    fastest) of a grid of numpy shape ([nz,] ny, nx); z = 0 in 2-D."""
+    idx = np.unravel_index(np.asarray(pix, dtype=np.int64), tuple(shape))[::-1]  # x, y[, z]
+    pos = np.zeros((len(pix), 3), dtype=np.float64)
+    for d, i in enumerate(idx):
+        pos[:, d] = float(origin[d]) + i.astype(np.float64) * float(h)
+    return pos
+
+
+def constant_table(shape, h, origin, sensors, pix, c0):
+    """T[s, j] = |x_j - r_s| / c0 for the nodes pix[j]; in 2-D only the
+    sensors' x and y count (the image plane)."""
+    sensors = np.asarray(sensors, dtype=np.float64)
+    nd = len(shape)
+    pos = node_positions(shape, h, origin, pix)[:, :nd]
+    out = np.empty((sensors.shape[0], len(pix)), dtype=np.float64)
+    for s in range(sensors.shape[0]):
+        diff = pos - sensors[s, :nd]
+        out[s] = np.sqrt(np.sum(diff * diff, axis=1)) / float(c0)
     return out
 
 

@@ -59,10 +59,29 @@ class BP:
 
     def __init__(self, speed, dx, origin, sensors, dt, n_samples, mask=None, weights=None,
                  flags=0, compact=False):
-        lib = _lib.load()
         speed = np.ascontiguousarray(speed, dtype=np.float32)
-        self.shape = speed.shape
-        self.grid = _lib.make_grid(speed.shape, dx, origin)
+        self._create(speed.shape, dx, origin, sensors, dt, n_samples, mask, weights, flags,
+                     compact, lambda lib, *args: lib.pat_bp_create(speed.ctypes.data, *args),
+                     "pat_bp_create")
+
+    @classmethod
+    def constant(cls, c0, shape, dx, origin, sensors, dt, n_samples, mask=None, weights=None,
+                 flags=0, compact=False):
+        """The conventional back projection (Sec. III's comparison method):
+        delays |r - r_s| / c0 for a constant sound speed c0 (m/s), computed in
+        the gather kernel; no travel-time table.  shape is the grid's
+        ([nz,] ny, nx); sensors may lie outside the grid."""
+        self = cls.__new__(cls)
+        self._create(tuple(shape), dx, origin, sensors, dt, n_samples, mask, weights, flags,
+                     compact, lambda lib, *args: lib.pat_bp_create_constant(float(c0), *args),
+                     "pat_bp_create_constant")
+        return self
+
+    def _create(self, shape, dx, origin, sensors, dt, n_samples, mask, weights, flags, compact,
+                create, what):
+        lib = _lib.load()
+        self.shape = tuple(shape)
+        self.grid = _lib.make_grid(self.shape, dx, origin)
         sensors = np.ascontiguousarray(sensors, dtype=np.float64)
         if sensors.ndim != 2 or sensors.shape[1] != 3:
             raise ValueError("sensors must be [ns, 3]")
@@ -70,17 +89,17 @@ class BP:
         self.n_samples = int(n_samples)
         self.dt = float(dt)
         m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
-        if m is not None and m.shape != speed.shape:
+        if m is not None and m.shape != self.shape:
             raise ValueError("mask must have the grid's shape")
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
         if compact:
             flags |= _lib.PAT_FLAG_COMPACT_OUT
         self.compact = bool(flags & _lib.PAT_FLAG_COMPACT_OUT)
         h = ctypes.c_void_p()
-        _lib.check(lib.pat_bp_create(speed.ctypes.data, ctypes.byref(self.grid), sensors.ctypes.data,
-                                     self.n_sensors, None if m is None else m.ctypes.data,
-                                     None if w is None else w.ctypes.data, self.dt, self.n_samples,
-                                     flags, ctypes.byref(h)), "pat_bp_create")
+        _lib.check(create(lib, ctypes.byref(self.grid), sensors.ctypes.data, self.n_sensors,
+                          None if m is None else m.ctypes.data,
+                          None if w is None else w.ctypes.data, self.dt, self.n_samples, flags,
+                          ctypes.byref(h)), what)
         self._h = h
         self._lib = lib
         inf = _lib.PatInfo()
@@ -232,13 +251,14 @@ class BP:
         _lib.check(self._lib.pat_bp_sync(self._h, _stream_ptr(stream)), "pat_bp_sync")
 
     def table(self):
-        """(u [tiles, ns, P] float32, base [tiles, ns] int32, slot [tiles*P] int32)."""
+        """(u [tiles, ns, P] float32, base [tiles, ns] int32, slot [tiles*P] int32);
+        u is None for a constant-speed handle (it stores no offsets)."""
         nt, ns, P = self.info["n_tiles"], self.n_sensors, self.info["tile_pix"]
-        u = np.empty((nt, ns, P), dtype=np.float32)
+        u = None if self.info["delays"] else np.empty((nt, ns, P), dtype=np.float32)
         b = np.empty((nt, ns), dtype=np.int32)
         s = np.empty(nt * P, dtype=np.int32)
-        _lib.check(self._lib.pat_bp_table(self._h, u.ctypes.data, b.ctypes.data, s.ctypes.data),
-                   "pat_bp_table")
+        _lib.check(self._lib.pat_bp_table(self._h, None if u is None else u.ctypes.data,
+                                          b.ctypes.data, s.ctypes.data), "pat_bp_table")
         return u, b, s
 
 

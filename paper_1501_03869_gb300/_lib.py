@@ -30,6 +30,7 @@ EXPORTS = (
     "pat_plan_info", "pat_plan_destroy", "pat_bp_reconstruct_multi", "pat_bp_autotune",
     "pat_bp_evict", "pat_bp_restore", "pat_srv_create", "pat_srv_register", "pat_srv_submit",
     "pat_srv_poll", "pat_srv_stats", "pat_srv_destroy", "pat_bp_reconstruct_noalloc",
+    "pat_bp_create_constant",
 )
 PAT_FLAG_HOST_MIRROR = 0x100
 PAT_PLAN_AUTOTUNE = 0x1
@@ -47,7 +48,8 @@ class PatInfo(ctypes.Structure):
                 ("n_samples_pad", ctypes.c_int), ("tile_pix", ctypes.c_int),
                 ("n_tiles", ctypes.c_int), ("window", ctypes.c_int), ("split", ctypes.c_int),
                 ("sensor_warps", ctypes.c_int), ("table_bytes", ctypes.c_int64),
-                ("build_seconds", ctypes.c_double)]
+                ("build_seconds", ctypes.c_double), ("delays", ctypes.c_int),
+                ("c0", ctypes.c_double)]
 
 
 class PatPlanInfo(ctypes.Structure):
@@ -105,6 +107,9 @@ def load():
         lib.pat_bp_create.restype = _i
         lib.pat_bp_create.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp, _vp, _d, _i, _u,
                                       ctypes.POINTER(_vp)]
+        lib.pat_bp_create_constant.restype = _i
+        lib.pat_bp_create_constant.argtypes = [_d, ctypes.POINTER(PatGrid), _vp, _i, _vp, _vp, _d,
+                                               _i, _u, ctypes.POINTER(_vp)]
         lib.pat_bp_reconstruct.restype = _i
         lib.pat_bp_reconstruct.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp]
         lib.pat_bp_preprocess.restype = _i

@@ -1,0 +1,108 @@
+// device.cuh -- PTX helpers shared by the kernels of the library (internal):
+// mbarriers with bounded waits, 1-D bulk copies, acquire/release atomics and
+// the named barriers of the gather kernel's unit hand-off.
+#pragma once
+
+#include <cstdint>
+
+namespace patbp {
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of `bar` with the given parity; false if it did not
+// complete within timeout_ns or another warp of the CTA already gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t timeout_ns, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (abort_flag && *abort_flag) return false;
+    if (global_ns() - t0 > timeout_ns) return false;
+  }
+}
+
+// 1-D bulk copy global -> shared of this CTA; completion counted in bytes on bar.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ int atomic_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__device__ __forceinline__ void named_barrier_arrive(int id, int threads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Hand-off barriers of the double-buffered unit sums, with literal ids so the
+// compiler reserves only the ids it sees: "full" 1/2 and "free" 3/4 per buffer.
+__device__ __forceinline__ void red_full_sync(int buf, int n) {
+  if (buf) asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
+  else asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void red_full_arrive(int buf, int n) {
+  if (buf) asm volatile("bar.arrive 2, %0;" ::"r"(n) : "memory");
+  else asm volatile("bar.arrive 1, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void red_free_sync(int buf, int n) {
+  if (buf) asm volatile("bar.sync 4, %0;" ::"r"(n) : "memory");
+  else asm volatile("bar.sync 3, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void red_free_arrive(int buf, int n) {
+  if (buf) asm volatile("bar.arrive 4, %0;" ::"r"(n) : "memory");
+  else asm volatile("bar.arrive 3, %0;" ::"r"(n) : "memory");
+}
+
+}  // namespace patbp

@@ -272,21 +272,11 @@ std::vector<int32_t> curve_order(const GridDesc& g, const uint8_t* mask) {
   return order;
 }
 
-// ------------------------------------------------------------ table build --
-bool build_table(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
-                 const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
-                 HostTable& out, std::string& err) {
-  auto t_start = std::chrono::steady_clock::now();
+// ------------------------------------------------------------ pixel layout --
+bool layout_pixels(const GridDesc& g, const uint8_t* mask, int P, bool compact_out, HostTable& out,
+                   std::vector<int32_t>& order, std::string& err) {
   const int64_t total = g.total();
-  std::vector<double> slowness_h(static_cast<size_t>(total));
-  for (int64_t v = 0; v < total; ++v) {
-    if (!(speed[v] > 0.0f) || !std::isfinite(speed[v])) {
-      err = "speed must be finite and > 0 at every node";
-      return false;
-    }
-    slowness_h[v] = g.dx / double(speed[v]);
-  }
-  std::vector<int32_t> order = curve_order(g, mask);
+  order = curve_order(g, mask);
   const int64_t n_pix = int64_t(order.size());
   if (n_pix == 0) {
     err = "mask selects no pixel";
@@ -295,7 +285,6 @@ bool build_table(const float* speed, const GridDesc& g, const double* sensors, i
   const int n_tiles = int((n_pix + P - 1) / P);
   out.P = P;
   out.n_tiles = n_tiles;
-  out.n_sensors = n_sensors;
   out.n_pix = n_pix;
   out.slot_dense.assign(size_t(n_tiles) * P, -1);
   out.slot_compact.assign(size_t(n_tiles) * P, -1);
@@ -320,6 +309,28 @@ bool build_table(const float* speed, const GridDesc& g, const double* sensors, i
       out.zero_runs.push_back(int32_t(v - s));
     }
   }
+  return true;
+}
+
+// ------------------------------------------------------------ table build --
+bool build_table(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
+                 const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
+                 HostTable& out, std::string& err) {
+  auto t_start = std::chrono::steady_clock::now();
+  const int64_t total = g.total();
+  std::vector<double> slowness_h(static_cast<size_t>(total));
+  for (int64_t v = 0; v < total; ++v) {
+    if (!(speed[v] > 0.0f) || !std::isfinite(speed[v])) {
+      err = "speed must be finite and > 0 at every node";
+      return false;
+    }
+    slowness_h[v] = g.dx / double(speed[v]);
+  }
+  std::vector<int32_t> order;
+  if (!layout_pixels(g, mask, P, compact_out, out, order, err)) return false;
+  const int64_t n_pix = out.n_pix;
+  const int n_tiles = out.n_tiles;
+  out.n_sensors = n_sensors;
   out.u.assign(size_t(n_tiles) * n_sensors * P, kOutOfRecord);
   out.base.assign(size_t(n_tiles) * n_sensors, 0);
   out.len.assign(size_t(n_tiles) * n_sensors, 0);

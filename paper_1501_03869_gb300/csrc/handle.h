@@ -37,6 +37,8 @@ struct pat_bp_s {
   unsigned flags = 0;
   bool compact = false;
   int P = 128, SW = 4, n_tiles = 0, W = 0;
+  int delays = 0;                     // 0 fast-marching table, 1 constant speed c0
+  double c0 = 0.0;
   int G = 64, n_seg = 1;              // sensors per segment, segments per tile
   int64_t n_pix = 0, grid_total = 0, out_stride = 0;
   int n_zero_runs = 0;
@@ -49,7 +51,9 @@ struct pat_bp_s {
   // launch shapes chosen by the autotuner: [frames-per-group index][format]
   int tuned_S[4][3] = {};
   int tuned_budget_kb[4][3] = {};
-  float* d_u = nullptr;
+  float* d_u = nullptr;               // table offsets (delays == 0)
+  float* d_anchor = nullptr;          // per (tile, sensor) anchors (delays == 1)
+  float4* d_pix = nullptr;            // per-pixel terms (delays == 1)
   int32_t* d_base = nullptr;
   int32_t* d_slot = nullptr;
   int32_t* d_zero_runs = nullptr;
@@ -72,10 +76,12 @@ struct pat_bp_s {
   size_t scales_cap = 0;
   float* d_out = nullptr;
   size_t out_cap = 0;
-  // pinned host copy of the device table (PAT_FLAG_HOST_MIRROR): u, base, slot,
-  // zero runs, weights; lets the device copy be dropped and reloaded
-  void* mirror[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t mirror_bytes[5] = {0, 0, 0, 0, 0};
+  // pinned host copy of the device table (PAT_FLAG_HOST_MIRROR): u (or the
+  // anchors), base, slot, zero runs, weights and the per-pixel terms (constant
+  // speed only); lets the device copy be dropped and reloaded
+  static constexpr int kMirrors = 6;
+  void* mirror[kMirrors] = {};
+  size_t mirror_bytes[kMirrors] = {};
   bool evicted = false;
   std::mutex mu;
 };

@@ -46,7 +46,9 @@ struct PreMultiParams {
 // (frame group, tile, segment of G sensors); units of all instances form one
 // sequence that the launch splits into contiguous ranges, one per CTA.
 struct InstDesc {
-  const float* u;           // [n_tiles][N_s][P] table offsets
+  const float* u;           // [n_tiles][N_s][P] table offsets (stored-table delays)
+  const float* anchor;      // [n_tiles][N_s_pad][8] per-sensor anchors (constant-speed delays)
+  const float4* pix;        // [n_tiles][P] pixel terms (2D, |D|^2) (constant-speed delays)
   const int32_t* base;      // [n_tiles][N_s_pad] window base | (window length << 16)
   const int32_t* slot;      // [n_tiles * P] output index, -1 = padding
   const int32_t* zero_runs; // (start, length) pairs of outputs to clear
@@ -79,6 +81,7 @@ struct GatherConfig {
   int SW = 4;       // sensor-phase warps
   int S = 16;       // sensors per stage
   int stages = 4;
+  int delays = 0;   // 0 stored table, 1 constant speed computed in the kernel
 };
 
 size_t gather_smem_bytes(const GatherConfig& c, int Wst);

@@ -82,6 +82,8 @@ static bool grid_from_abi(const pat_grid* pg, GridDesc& g, std::string& err) {
 static void free_handle(pat_bp_t h) {
   if (!h) return;
   cudaFree(h->d_u);
+  cudaFree(h->d_anchor);
+  cudaFree(h->d_pix);
   cudaFree(h->d_base);
   cudaFree(h->d_slot);
   cudaFree(h->d_zero_runs);
@@ -95,7 +97,7 @@ static void free_handle(pat_bp_t h) {
   cudaFree(h->d_sig);
   cudaFree(h->d_scales);
   cudaFree(h->d_out);
-  for (int i = 0; i < 5; ++i) cudaFreeHost(h->mirror[i]);
+  for (int i = 0; i < pat_bp_s::kMirrors; ++i) cudaFreeHost(h->mirror[i]);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }
@@ -109,31 +111,29 @@ static pat_status upload(T** dst, const std::vector<T>& src, const char* what) {
   return PAT_OK;
 }
 
-extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* grid,
-                                    const double* sensors_host, int n_sensors,
-                                    const uint8_t* mask_host, const float* weights_host,
-                                    double dt, int n_samples, unsigned flags, pat_bp_t* out) {
-  if (!out) return fail(PAT_ERR_INVALID, "out is NULL");
-  *out = nullptr;
-  if (!speed_host || !sensors_host) return fail(PAT_ERR_INVALID, "speed/sensors NULL");
+// Checks shared by both create calls.
+static pat_status check_create_args(const pat_grid* grid, const double* sensors_host, int n_sensors,
+                                    double dt, int n_samples, GridDesc& g) {
+  if (!sensors_host) return fail(PAT_ERR_INVALID, "sensors NULL");
   if (n_sensors < 1 || n_sensors > (1 << 20)) return fail(PAT_ERR_INVALID, "n_sensors out of range");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(PAT_ERR_INVALID, "dt must be > 0");
   if (n_samples < 2 || n_samples > 32768) return fail(PAT_ERR_INVALID, "n_samples must be 2..32768");
-  GridDesc g;
   std::string err;
   if (!grid_from_abi(grid, g, err)) return fail(PAT_ERR_INVALID, err);
-  for (int s = 0; s < n_sensors; ++s)
-    for (int d = 0; d < g.ndim; ++d) {
-      double x = (sensors_host[3 * s + d] - g.origin[d]) / g.dx;
-      if (!(x >= 0.0 && x <= double(g.n[d] - 1)))
-        return fail(PAT_ERR_INVALID, "sensor " + std::to_string(s) + " lies outside the grid");
-    }
+  return PAT_OK;
+}
 
+static pat_status new_handle(const GridDesc& g, int n_sensors, int n_samples, double dt,
+                             unsigned flags, pat_bp_t* out) {
   pat_bp_t h = new (std::nothrow) pat_bp_s();
   if (!h) return fail(PAT_ERR_OOM, "handle");
-  PAT_CUDA(cudaGetDevice(&h->device));
   cudaDeviceProp prop;
-  PAT_CUDA(cudaGetDeviceProperties(&prop, h->device));
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "device properties");
+  }
   h->n_sm = prop.multiProcessorCount;
   h->max_smem = int(prop.sharedMemPerBlockOptin);
   h->g = g;
@@ -147,13 +147,14 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
   h->P = (flags & PAT_FLAG_TILE_256) ? 256 : 128;
   h->SW = h->P == 128 ? 4 : 2;
   h->grid_total = g.total();
+  *out = h;
+  return PAT_OK;
+}
 
-  HostTable tab;
-  if (!build_table(speed_host, g, sensors_host, n_sensors, mask_host, dt, n_samples, h->P,
-                   h->compact, tab, err)) {
-    free_handle(h);
-    return fail(PAT_ERR_INVALID, err);
-  }
+// Upload the built layout and finish the handle (frees it on failure).
+static pat_status finish_create(pat_bp_t h, const HostTable& tab, const float* weights_host,
+                                pat_bp_t* out) {
+  const int n_sensors = h->ns;
   h->n_tiles = tab.n_tiles;
   h->n_pix = tab.n_pix;
   h->W = tab.W;
@@ -180,22 +181,34 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
       const size_t i = size_t(t) * n_sensors + s;
       packed[size_t(t) * h->ns_pad + s] = int32_t(uint32_t(tab.base[i]) | (uint32_t(tab.len[i]) << 16));
     }
+  // constant speed: anchors padded to N_s_pad rows per tile like the bases
+  std::vector<float> anchor;
+  if (h->delays) {
+    anchor.assign(size_t(h->n_tiles) * h->ns_pad * 8, 0.0f);
+    for (int t = 0; t < h->n_tiles; ++t)
+      std::memcpy(anchor.data() + size_t(t) * h->ns_pad * 8,
+                  tab.anchor.data() + size_t(t) * n_sensors * 8, size_t(n_sensors) * 8 * 4);
+  }
+  const std::vector<float>& delay_data = h->delays ? anchor : tab.u;
+  const std::vector<int32_t>& slots = h->compact ? tab.slot_compact : tab.slot_dense;
   pat_status st;
-  if ((st = upload(&h->d_u, tab.u, "table")) != PAT_OK ||
+  if ((st = upload(h->delays ? &h->d_anchor : &h->d_u, delay_data, "delay data")) != PAT_OK ||
+      (h->delays && (st = upload(reinterpret_cast<float**>(&h->d_pix), tab.pixq, "pixel terms")) != PAT_OK) ||
       (st = upload(&h->d_base, packed, "bases")) != PAT_OK ||
-      (st = upload(&h->d_slot, h->compact ? tab.slot_compact : tab.slot_dense, "slots")) != PAT_OK ||
+      (st = upload(&h->d_slot, slots, "slots")) != PAT_OK ||
       (st = upload(&h->d_zero_runs, tab.zero_runs, "zero runs")) != PAT_OK ||
       (st = upload(&h->d_w, w, "weights")) != PAT_OK) {
     free_handle(h);
     return st;
   }
-  if (flags & PAT_FLAG_HOST_MIRROR) {
-    const void* src[5] = {tab.u.data(), packed.data(),
-                          (h->compact ? tab.slot_compact : tab.slot_dense).data(),
-                          tab.zero_runs.data(), w.data()};
-    const size_t bytes[5] = {tab.u.size() * 4, packed.size() * 4, tab.slot_dense.size() * 4,
-                             std::max<size_t>(tab.zero_runs.size(), 1) * 4, w.size() * 4};
-    for (int i = 0; i < 5; ++i) {
+  if (h->flags & PAT_FLAG_HOST_MIRROR) {
+    const void* src[pat_bp_s::kMirrors] = {delay_data.data(), packed.data(), slots.data(),
+                                           tab.zero_runs.data(), w.data(), tab.pixq.data()};
+    const size_t bytes[pat_bp_s::kMirrors] = {
+        std::max<size_t>(delay_data.size(), 1) * 4, packed.size() * 4, slots.size() * 4,
+        std::max<size_t>(tab.zero_runs.size(), 1) * 4, w.size() * 4, tab.pixq.size() * 4};
+    for (int i = 0; i < pat_bp_s::kMirrors; ++i) {
+      if (bytes[i] == 0) continue;  // no per-pixel terms for a stored table
       if (cudaMallocHost(&h->mirror[i], bytes[i]) != cudaSuccess) {
         free_handle(h);
         return fail(PAT_ERR_OOM, "pinned host mirror");
@@ -221,6 +234,59 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
   }
   *out = h;
   return PAT_OK;
+}
+
+extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* grid,
+                                    const double* sensors_host, int n_sensors,
+                                    const uint8_t* mask_host, const float* weights_host,
+                                    double dt, int n_samples, unsigned flags, pat_bp_t* out) {
+  if (!out) return fail(PAT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!speed_host) return fail(PAT_ERR_INVALID, "speed NULL");
+  GridDesc g;
+  pat_status st = check_create_args(grid, sensors_host, n_sensors, dt, n_samples, g);
+  if (st != PAT_OK) return st;
+  for (int s = 0; s < n_sensors; ++s)
+    for (int d = 0; d < g.ndim; ++d) {
+      double x = (sensors_host[3 * s + d] - g.origin[d]) / g.dx;
+      if (!(x >= 0.0 && x <= double(g.n[d] - 1)))
+        return fail(PAT_ERR_INVALID, "sensor " + std::to_string(s) + " lies outside the grid");
+    }
+  pat_bp_t h = nullptr;
+  if ((st = new_handle(g, n_sensors, n_samples, dt, flags, &h)) != PAT_OK) return st;
+  HostTable tab;
+  std::string err;
+  if (!build_table(speed_host, g, sensors_host, n_sensors, mask_host, dt, n_samples, h->P,
+                   h->compact, tab, err)) {
+    free_handle(h);
+    return fail(PAT_ERR_INVALID, err);
+  }
+  return finish_create(h, tab, weights_host, out);
+}
+
+extern "C" pat_status pat_bp_create_constant(double c0, const pat_grid* grid,
+                                             const double* sensors_host, int n_sensors,
+                                             const uint8_t* mask_host, const float* weights_host,
+                                             double dt, int n_samples, unsigned flags,
+                                             pat_bp_t* out) {
+  if (!out) return fail(PAT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!(c0 > 0.0) || !std::isfinite(c0)) return fail(PAT_ERR_INVALID, "c0 must be finite and > 0");
+  GridDesc g;
+  pat_status st = check_create_args(grid, sensors_host, n_sensors, dt, n_samples, g);
+  if (st != PAT_OK) return st;
+  pat_bp_t h = nullptr;
+  if ((st = new_handle(g, n_sensors, n_samples, dt, flags, &h)) != PAT_OK) return st;
+  h->delays = 1;
+  h->c0 = c0;
+  HostTable tab;
+  std::string err;
+  if (!build_constant_layout(c0, g, sensors_host, n_sensors, mask_host, dt, n_samples, h->P,
+                             h->compact, tab, err)) {
+    free_handle(h);
+    return fail(PAT_ERR_INVALID, err);
+  }
+  return finish_create(h, tab, weights_host, out);
 }
 
 namespace patbp {
@@ -289,6 +355,7 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
   GatherConfig c;
   c.P = h->P;
   c.SW = h->SW;
+  c.delays = h->delays;
   c.FB = FB;
   c.S = S;
   c.stages = 6;
@@ -345,6 +412,8 @@ InstDesc make_desc(pat_bp_t h, float* out, int n_frames, int FB, int wst) {
   InstDesc d;
   std::memset(&d, 0, sizeof(d));
   d.u = h->d_u;
+  d.anchor = h->d_anchor;
+  d.pix = h->d_pix;
   d.base = h->d_base;
   d.slot = h->d_slot;
   d.zero_runs = h->d_zero_runs;
@@ -370,7 +439,7 @@ InstDesc make_desc(pat_bp_t h, float* out, int n_frames, int FB, int wst) {
 
 int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm) {
   struct Key {
-    int P, FB, SW, S, stages, fmt, wst;
+    int P, FB, SW, S, stages, fmt, wst, delays;
   };
   static std::mutex mu;
   static std::vector<std::pair<Key, int>> cache;
@@ -378,11 +447,11 @@ int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm) {
   for (auto& e : cache) {
     const Key& k = e.first;
     if (k.P == c.P && k.FB == c.FB && k.SW == c.SW && k.S == c.S && k.stages == c.stages &&
-        k.fmt == fmt && k.wst == wst)
+        k.fmt == fmt && k.wst == wst && k.delays == c.delays)
       return e.second;
   }
   const int r = gather_resident_ctas(c, fmt, wst, n_sm);
-  cache.push_back({Key{c.P, c.FB, c.SW, c.S, c.stages, fmt, wst}, r});
+  cache.push_back({Key{c.P, c.FB, c.SW, c.S, c.stages, fmt, wst, c.delays}, r});
   return r;
 }
 
@@ -390,8 +459,14 @@ int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm) {
 
 namespace patbp {
 
+// device bytes of the delay data: table offsets, or anchors and pixel terms
+static size_t delay_bytes(pat_bp_t h) {
+  if (h->delays) return size_t(h->n_tiles) * h->ns_pad * 32 + size_t(h->n_tiles) * h->P * 16;
+  return size_t(h->n_tiles) * h->ns * h->P * 4;
+}
+
 size_t table_device_bytes(pat_bp_t h) {
-  return size_t(h->n_tiles) * h->ns * h->P * 4 + size_t(h->n_tiles) * h->ns_pad * 4 +
+  return delay_bytes(h) + size_t(h->n_tiles) * h->ns_pad * 4 +
          size_t(h->n_tiles) * h->P * 4 + std::max<size_t>(size_t(h->n_zero_runs) * 2, 1) * 4 +
          size_t(h->ns) * 4;
 }
@@ -405,10 +480,11 @@ pat_status evict_locked(pat_bp_t h) {
   if (!h->mirror[0]) return fail(PAT_ERR_INVALID, "eviction needs PAT_FLAG_HOST_MIRROR");
   if (h->evicted) return PAT_OK;
   PAT_CUDA(cudaDeviceSynchronize());
-  void** dev[9] = {reinterpret_cast<void**>(&h->d_u), reinterpret_cast<void**>(&h->d_base),
-                   reinterpret_cast<void**>(&h->d_slot), reinterpret_cast<void**>(&h->d_zero_runs),
-                   reinterpret_cast<void**>(&h->d_w), &h->d_b, reinterpret_cast<void**>(&h->d_m),
-                   reinterpret_cast<void**>(&h->d_part), reinterpret_cast<void**>(&h->d_counter)};
+  void** dev[11] = {reinterpret_cast<void**>(&h->d_u), reinterpret_cast<void**>(&h->d_anchor),
+                    reinterpret_cast<void**>(&h->d_pix), reinterpret_cast<void**>(&h->d_base),
+                    reinterpret_cast<void**>(&h->d_slot), reinterpret_cast<void**>(&h->d_zero_runs),
+                    reinterpret_cast<void**>(&h->d_w), &h->d_b, reinterpret_cast<void**>(&h->d_m),
+                    reinterpret_cast<void**>(&h->d_part), reinterpret_cast<void**>(&h->d_counter)};
   for (void** p : dev) {
     cudaFree(*p);
     *p = nullptr;
@@ -421,10 +497,13 @@ pat_status evict_locked(pat_bp_t h) {
 
 pat_status restore_locked(pat_bp_t h, cudaStream_t st) {
   if (!h->evicted) return PAT_OK;
-  void** dev[5] = {reinterpret_cast<void**>(&h->d_u), reinterpret_cast<void**>(&h->d_base),
-                   reinterpret_cast<void**>(&h->d_slot), reinterpret_cast<void**>(&h->d_zero_runs),
-                   reinterpret_cast<void**>(&h->d_w)};
-  for (int i = 0; i < 5; ++i) {
+  void** dev[pat_bp_s::kMirrors] = {
+      h->delays ? reinterpret_cast<void**>(&h->d_anchor) : reinterpret_cast<void**>(&h->d_u),
+      reinterpret_cast<void**>(&h->d_base), reinterpret_cast<void**>(&h->d_slot),
+      reinterpret_cast<void**>(&h->d_zero_runs), reinterpret_cast<void**>(&h->d_w),
+      reinterpret_cast<void**>(&h->d_pix)};
+  for (int i = 0; i < pat_bp_s::kMirrors; ++i) {
+    if (!h->mirror[i]) continue;
     if (cudaMalloc(dev[i], h->mirror_bytes[i]) != cudaSuccess) {
       for (int j = 0; j <= i; ++j) {
         cudaFree(*dev[j]);
@@ -627,8 +706,10 @@ extern "C" pat_status pat_bp_info(pat_bp_t h, pat_bp_info_t* info) {
   info->window = h->W;
   info->split = h->n_seg;
   info->sensor_warps = h->SW;
-  info->table_bytes = int64_t(h->n_tiles) * h->ns * h->P * 4;
+  info->table_bytes = int64_t(delay_bytes(h));
   info->build_seconds = h->build_seconds;
+  info->delays = h->delays;
+  info->c0 = h->c0;
   return PAT_OK;
 }
 
@@ -636,6 +717,8 @@ extern "C" pat_status pat_bp_table(pat_bp_t h, float* u_host, int32_t* base_host
   if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
   PAT_CUDA(cudaSetDevice(h->device));
   const size_t n = size_t(h->n_tiles) * h->ns;
+  if (u_host && h->delays)
+    return fail(PAT_ERR_INVALID, "a constant-speed handle stores no travel-time table");
   if (u_host) PAT_CUDA(cudaMemcpy(u_host, h->d_u, n * h->P * 4, cudaMemcpyDeviceToHost));
   if (base_host) {
     std::vector<int32_t> packed(size_t(h->n_tiles) * h->ns_pad);

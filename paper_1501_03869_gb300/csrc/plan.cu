@@ -64,6 +64,7 @@ pat_status plan_shape(pat_plan_t pl, int FB, int S, int budget_kb) {
   GatherConfig c;
   c.P = pl->P;
   c.SW = pl->SW;
+  c.delays = pl->hs[0]->delays;
   c.FB = FB;
   c.S = S;
   c.stages = 6;
@@ -344,6 +345,9 @@ static pat_status plan_new(const pat_bp_t* handles, const int* n_frames, int n, 
       if (handles[j] == handles[i]) return fail(PAT_ERR_INVALID, "a handle appears twice in one plan");
     if (handles[i]->device != handles[0]->device || handles[i]->P != handles[0]->P)
       return fail(PAT_ERR_INVALID, "plan handles must share the device and the tile size");
+    if (handles[i]->delays != handles[0]->delays)
+      return fail(PAT_ERR_INVALID,
+                  "plan handles must share the delay source (stored table or constant speed)");
   }
   std::unique_ptr<pat_plan_s> pl(new (std::nothrow) pat_plan_s());
   if (!pl) return fail(PAT_ERR_OOM, "plan");

@@ -48,6 +48,9 @@ struct HostTable {
   std::vector<int32_t> slot_dense;  // [n_tiles * P] dense grid index or -1
   std::vector<int32_t> slot_compact;// [n_tiles * P] raster rank among mask pixels or -1
   std::vector<int32_t> zero_runs;   // pairs (start, length) of non-mask runs of the grid
+  // constant-speed delays (build_constant_layout): no u; instead
+  std::vector<float> anchor;        // [n_tiles][n_sensors][8] per-sensor anchor of each tile
+  std::vector<float> pixq;          // [n_tiles][P][4] per-pixel terms relative to the anchor
   double build_seconds = 0.0;
 };
 
@@ -89,5 +92,20 @@ bool build_table(const float* speed, const GridDesc& g, const double* sensors, i
 // Pixel order used by the table: mask pixels (dense indices) sorted along the
 // space-filling curve of the grid.
 std::vector<int32_t> curve_order(const GridDesc& g, const uint8_t* mask);
+
+// Tiles of the curve order: sets P, n_tiles, n_pix, both slot maps and the
+// zero runs of `out`; `order` receives the curve order.  False if the mask is empty.
+bool layout_pixels(const GridDesc& g, const uint8_t* mask, int P, bool compact_out, HostTable& out,
+                   std::vector<int32_t>& order, std::string& err);
+
+// Constant-speed delays (the conventional back projection, Sec. II-C):
+// T_s(r) = |r - r_s| / c0, nothing stored per pixel and sensor.  Fills the
+// pixel layout, the windows (base, len, W) exactly as build_table would for
+// these delays (with a 1e-3-sample margin on both ends for the kernel's FP32
+// evaluation), the anchors and the per-pixel terms.  Sensors may lie anywhere
+// (inside the grid box or not); in 2-D only their x and y count.
+bool build_constant_layout(double c0, const GridDesc& g, const double* sensors, int n_sensors,
+                           const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
+                           HostTable& out, std::string& err);
 
 }  // namespace patbp

@@ -453,14 +453,72 @@ def test_p9_skull_fmm_beats_constant_speed():
     pix = np.flatnonzero(w.mask.ravel())
     T = oracle.travel_table(w.speed, w.dx, w.origin, w.sensors, pix)
     img_fmm = oracle.reconstruct(w.speed, w.dx, w.origin, w.sensors, p, w.dt, w.mask, T=T)
-    coords = np.stack(np.unravel_index(pix, w.speed.shape)[::-1], axis=1) * w.dx + w.origin
-    dist = np.linalg.norm(coords[None, :, :] - w.sensors[:, None, :2], axis=2)
-    img_c = oracle.reconstruct(w.speed, w.dx, w.origin, w.sensors, p, w.dt, w.mask,
-                               T=dist / g["c_constant_bp"])
+    Tc = oracle.constant_table(w.speed.shape, w.dx, w.origin, w.sensors, pix, g["c_constant_bp"])
+    img_c = oracle.reconstruct(w.speed, w.dx, w.origin, w.sensors, p, w.dt, w.mask, T=Tc)
     p0 = synth.phantom_discs(w.speed.shape, w.dx, w.origin, centre, [1.5 * w.dx], [1.0])
     e_fmm, e_c = _peak_error(img_fmm, p0), _peak_error(img_c, p0)
     assert e_fmm <= 1.0 and e_c > 3.0
     assert 0.9 < img_fmm.max() < 1.1 and img_c.max() < 0.5
+
+
+# ------------------------------------------- constant-speed time of flight --
+def test_constant_table_pythagorean_offsets_are_exact():
+    """Conventional BP delays (Sec. II-C): node offsets (3, 4) and (2, 3, 6)
+    node spacings from a sensor give 5 and 7 spacings over c0 exactly; in 2-D
+    the sensor's z does not count."""
+    h, c0 = 0.25e-3, 1560.0
+    origin = (-1.0e-3, 2.0e-3, 0.5e-3)
+    # 2-D: grid (ny, nx) = (9, 11); sensor on node (x=1, y=2) lifted off-plane
+    sens = np.array([[origin[0] + 1 * h, origin[1] + 2 * h, 7.0e-3]])
+    T = oracle.constant_table((9, 11), h, origin, sens, [6 * 11 + 4], c0)
+    assert T[0, 0] * c0 / h == pytest.approx(5.0, rel=1e-15)
+    T0 = oracle.constant_table((9, 11), h, origin, sens, [2 * 11 + 1], c0)
+    assert T0[0, 0] == 0.0
+    # 3-D: grid (nz, ny, nx) = (8, 6, 5); sensor on node (x=0, y=1, z=0)
+    sens3 = np.array([[origin[0], origin[1] + h, origin[2]]])
+    T3 = oracle.constant_table((8, 6, 5), h, origin, sens3, [(6 * 6 + 4) * 5 + 2], c0)
+    assert T3[0, 0] * c0 / h == pytest.approx(7.0, rel=1e-15)
+
+
+def test_constant_table_is_the_homogeneous_fast_marching_limit():
+    """In a homogeneous medium the fast-marching table (Sec. II-B) converges
+    to the constant-speed delays, from above, at first order in dx."""
+    c0, L = 1560.0, 1.0e-3
+    src = np.array([[0.21e-4, -0.37e-4, 0.0]])
+    errs = []
+    for n in (33, 65, 129):
+        h = 2 * L / (n - 1)
+        origin = (-L, -L, 0.0)
+        pix = np.arange(n * n)
+        Tf = oracle.travel_table(np.full((n, n), c0), h, origin, src, pix)
+        Tc = oracle.constant_table((n, n), h, origin, src, pix, c0)
+        err = Tf - Tc
+        assert err.min() > -1e-12 * Tc.max()
+        errs.append(err.max())
+    assert errs[1] < 0.8 * errs[0] and errs[2] < 0.8 * errs[1]
+
+
+def test_constant_speed_bp_of_homogeneous_absorber_recovers_it():
+    """With the true constant speed the straight-ray delays are exact, and the
+    Eq. (BP) integrand of a uniform absorber's N-shaped pulse is its amplitude
+    inside it: the conventional back projection gives the amplitude at the
+    absorber's node and its maximum lies inside the absorber."""
+    n, h, c0 = 64, 0.2e-3, 1540.0
+    shape = (n, n)
+    sp = np.full(shape, c0, dtype=np.float32)
+    origin = synth.centred_origin(shape, h)
+    sensors = synth.ring_sensors(64, 30 * h)
+    centre = np.array([[origin[0] + 26 * h, origin[1] + 36 * h, 0.0]])
+    dt, nt = 20e-9, 800
+    p = synth.render_signals(sp, h, origin, sensors, centre, [2.0 * h], [1.0], dt, nt, 0.0,
+                             np.random.default_rng(3))
+    pix = np.arange(n * n)
+    T = oracle.constant_table(shape, h, origin, sensors, pix, c0)
+    img = oracle.reconstruct(sp, h, origin, sensors, p, dt, T=T)
+    assert img[36, 26] == pytest.approx(1.0, abs=1e-3)
+    iy, ix = np.unravel_index(np.argmax(img), shape)
+    assert math.hypot(ix - 26, iy - 36) <= 2.0
+    assert img.max() < 1.0 + 1e-3
 
 
 # ------------------------------------------------------ paper's numbers --
