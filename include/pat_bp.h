@@ -63,6 +63,10 @@ typedef void* pat_stream_t; /* a cudaStream_t; NULL = legacy default stream */
 #define PAT_FLAG_TILE_256 0x20u   /* force 256 pixels per tile                   */
 #define PAT_FLAG_HOST_MIRROR 0x100u /* keep a pinned host copy of the table so the
                                        device copy can be evicted and restored    */
+#define PAT_FLAG_STAGED_SINGLE 0x200u /* single frames through the staged (TMA
+                                         pipeline) gather too; by default one
+                                         frame takes the unstaged kernel, which
+                                         gives the same bits                     */
 
 /* Read-only facts about a handle (pat_bp_info). */
 typedef struct {

@@ -33,6 +33,7 @@ EXPORTS = (
     "pat_bp_create_constant",
 )
 PAT_FLAG_HOST_MIRROR = 0x100
+PAT_FLAG_STAGED_SINGLE = 0x200
 PAT_PLAN_AUTOTUNE = 0x1
 PAT_PLAN_GRAPH = 0x2
 

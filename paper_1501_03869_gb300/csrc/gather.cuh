@@ -17,6 +17,11 @@
 //   result depends neither on timing nor on how frames or instances are
 //   batched.
 //
+// The kernel is launched as a programmatic dependent of the preprocessing grid
+// and may start before it finishes; lines an earlier kernel left in an SM's L1
+// are then not reliably dropped, so its plain global loads use ld.global.cg
+// (L2 only) and everything else arrives by bulk copies, which read L2.
+//
 // Every wait on an mbarrier is bounded by a wall-clock limit; on expiry the CTA
 // records kStatusTimeout, drains its own copies in flight (bounded again) and
 // exits without touching the output's remaining values.
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), DELAYS ? (FB == 1 ?
       if constexpr (DELAYS != 0) {
         const float4* src = p.inst[q.inst].pix + int64_t(q.tile) * P + pg * 128 + lane;
 #pragma unroll
-        for (int x = 0; x < 4; ++x) pq[x] = __ldg(src + x * 32);
+        for (int x = 0; x < 4; ++x) pq[x] = __ldcg(src + x * 32);
       }
       float acc[FB][4];
 #pragma unroll
@@ -523,7 +528,7 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), DELAYS ? (FB == 1 ?
       red_free_arrive(ew, (NWC + 1) * 32);  // red[ew] free again
       int slot_idx[KO];
 #pragma unroll
-      for (int k = 0; k < KO; ++k) slot_idx[k] = __ldg(d.slot + int64_t(q.tile) * P + k * 32 + lane);
+      for (int k = 0; k < KO; ++k) slot_idx[k] = __ldcg(d.slot + int64_t(q.tile) * P + k * 32 + lane);
       const int64_t pbase = ((int64_t(q.fg) * d.n_tiles + q.tile) * d.n_seg) * FB * P;
       if (d.n_seg == 1) {
 #pragma unroll

@@ -1,0 +1,315 @@
+// gather_direct.cu -- the single-frame gather of Eq. (BP) without staging.
+//
+// Two launches.  The gather kernel is persistent: CTA c takes units (tile,
+// segment of G sensors) c, c + grid, c + 2 grid, ... in tile-major order, and
+// asks L2 for each unit's delay data two units ahead with one bulk prefetch.
+// Its warps are the (pixel group, sensor phase) pairs of the staged kernel's
+// consumers; a warp reads the delay data (table offsets, or the constant-
+// speed anchors) and the window bases for a chunk of its sensors, then
+// gathers the integrand rows from L2 with loads that never branch (an arrival
+// after the record reads a zero padding row), and finally stores its phase
+// sums -- no barrier, fence or atomic anywhere, so no warp ever waits for
+// another.  The reduction kernel then forms every pixel's sum over phases and
+// segments and scatters it to the image.
+//
+// Both kernels are launched as programmatic dependents, which can start before
+// the kernels ahead of them in the stream have finished; lines that an earlier
+// kernel left in an SM's L1 are then not reliably dropped, so every global load
+// here goes through L2 only (ld.global.cg), never the non-coherent L1 path.
+//
+// Arithmetic and summation order are those of the staged kernel with one
+// frame per unit (gather.cuh): phase sp of a segment accumulates sensors
+// s_lo + sp, s_lo + sp + SW, ... with acc = fma(m_s, fma(ph, b1 - b0, b0), acc),
+// phases are summed in order 0..SW-1 and segments in order 0..n_seg-1.  A frame
+// therefore gives the same bits here as inside any batch that the staged kernel
+// reconstructs.
+#include <algorithm>
+
+#include "gather.cuh"
+
+namespace patbp {
+
+namespace {
+
+constexpr int kDirectChunk = 1;    // sensors of a phase whose loads are issued together
+constexpr int kDirectMinCtas = 8;  // resident CTAs per SM the registers must allow
+
+struct DirectParams {
+  const float* u;
+  const float* anchor;
+  const float4* pix;
+  const int32_t* base;
+  const int32_t* slot;
+  const int32_t* zero_runs;
+  const void* b;
+  const float* m;
+  float* out;
+  float* part;  // [n_tiles][n_seg][SW][P] phase sums
+  int n_zero_runs, n_sensors, n_sensors_pad, n_t_pad, n_tiles, n_seg, G;
+};
+
+// One sensor's contribution to this lane's 4 pixels; `row` points at the
+// sensor's window base in the integrand.  Offsets above `cap` are after the
+// record: they read the zero row `zrow` (a padding row after the record) with
+// phase 0, which adds m * 0 exactly as the staged kernel's zero rows do.
+template <int FMT>
+__device__ __forceinline__ void direct_accumulate(float (&acc)[4], const float (&uu)[4], float cap,
+                                                  const uint32_t* row, unsigned zrow, float mm) {
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const bool in = uu[x] <= cap;
+    const unsigned t = unsigned(__float2int_rz(uu[x]));
+    const unsigned i = in ? t : zrow;
+    const float ph = in ? uu[x] - float(t) : 0.0f;
+    const uint32_t w0 = __ldcg(row + i);
+    if constexpr (FMT == kBF32) {
+      const float b0 = __uint_as_float(w0), b1 = __uint_as_float(__ldcg(row + i + 1));
+      acc[x] = fmaf(mm, fmaf(ph, b1 - b0, b0), acc[x]);
+    } else if constexpr (FMT == kBBF16P) {
+      const float v = fmaf(ph, __uint_as_float(w0 & 0xffff0000u), __uint_as_float(w0 << 16));
+      acc[x] = fmaf(mm, v, acc[x]);
+    } else {
+      const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&w0));
+      acc[x] = fmaf(mm, fmaf(ph, h.y, h.x), acc[x]);
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// Pull the delay data of `unit` (one contiguous block) into L2.
+template <int P, int DELAYS>
+__device__ __forceinline__ void prefetch_unit(const DirectParams& p, int64_t unit, int64_t n_units) {
+  if (unit >= n_units) return;
+  const int tile = int(unit / p.n_seg), seg = int(unit - int64_t(tile) * p.n_seg);
+  const int s_lo = seg * p.G, n = min(p.n_sensors, s_lo + p.G) - s_lo;
+  if constexpr (DELAYS == 0)
+    bulk_prefetch_l2(p.u + (int64_t(tile) * p.n_sensors + s_lo) * P, uint32_t(n) * P * 4);
+  else
+    bulk_prefetch_l2(p.anchor + (int64_t(tile) * p.n_sensors_pad + s_lo) * 8, uint32_t(n) * 32);
+}
+
+template <int P, int SW, int FMT, int DELAYS>
+__global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
+    gather_direct_kernel(const __grid_constant__ DirectParams p) {
+  constexpr int PW = P / 128;
+  constexpr int CH = kDirectChunk;
+  // the reduction kernel may start now; it waits for this grid's results
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pg = warp % PW, sp = warp / PW;
+  const int px0 = pg * 128 + lane;
+  const int64_t n_units = int64_t(p.n_tiles) * p.n_seg;
+  if (threadIdx.x == 0) {
+    prefetch_unit<P, DELAYS>(p, blockIdx.x, n_units);
+    prefetch_unit<P, DELAYS>(p, int64_t(blockIdx.x) + gridDim.x, n_units);
+  }
+  const uint32_t* bsrc = static_cast<const uint32_t*>(p.b);
+  bool waited = false;
+  for (int64_t unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+    if (threadIdx.x == 0) prefetch_unit<P, DELAYS>(p, unit + 2 * int64_t(gridDim.x), n_units);
+    const int tile = int(unit / p.n_seg);
+    const int seg = int(unit - int64_t(tile) * p.n_seg);
+    const int s_lo = seg * p.G, s_hi = min(p.n_sensors, s_lo + p.G);
+    float4 pq[4];
+    if constexpr (DELAYS != 0) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x) pq[x] = __ldcg(p.pix + int64_t(tile) * P + px0 + x * 32);
+    }
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // Sensors of this phase in chunks of CH: the loads that do not depend on
+    // the preprocessing (delay data, window bases) are issued for the chunk
+    // first -- for the first chunk before waiting for the preprocessing grid.
+    for (int c0 = s_lo + sp; c0 < s_hi; c0 += CH * SW) {
+      uint32_t bw[CH];
+      float uu[CH][4];
+      float4 an[DELAYS ? CH : 1][2];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const int s = c0 + j * SW;
+        const bool ok = s < s_hi;
+        bw[j] = ok ? uint32_t(__ldcg(p.base + int64_t(tile) * p.n_sensors_pad + s)) : 0u;
+        if constexpr (DELAYS == 0) {
+          const float* urow = p.u + (int64_t(tile) * p.n_sensors + s) * P + px0;
+#pragma unroll
+          for (int x = 0; x < 4; ++x) uu[j][x] = ok ? __ldcg(urow + x * 32) : kFarOffset;
+        } else {
+          const float4* ap = reinterpret_cast<const float4*>(p.anchor) +
+                             (int64_t(tile) * p.n_sensors_pad + (ok ? s : s_lo)) * 2;
+          an[j][0] = __ldcg(ap);
+          an[j][1] = __ldcg(ap + 1);
+          if (!ok) an[j][1].y = -1.0f;  // cap below every offset: nothing to add
+        }
+      }
+      if (!waited) {
+        // integrand and multipliers come from the preprocessing grid
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        waited = true;
+      }
+      float mm[CH];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) mm[j] = c0 + j * SW < s_hi ? __ldcg(p.m + c0 + j * SW) : 0.0f;
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const int s = min(c0 + j * SW, s_hi - 1);
+        if constexpr (DELAYS != 0) {
+          const float4 A = an[j][0], B = an[j][1];
+          if (B.w == 0.0f) {
+            const float m2u0 = -2.0f * A.w;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              const float num =
+                  fmaf(pq[x].x, A.x, fmaf(pq[x].y, A.y, fmaf(pq[x].z, A.z, pq[x].w)));
+              const float sq = num + B.z;
+              const float y = rsqrtf(sq);
+              const float da = sq * y - A.w;
+              const float r = fmaf(-da, da, fmaf(m2u0, da, num));
+              const float v = fmaf(r, 0.5f * y, da) + B.x;
+              uu[j][x] = v > B.y ? kFarOffset : fmaxf(v, 0.0f);
+            }
+          } else {
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              const float d0 = fmaf(0.5f, pq[x].x, A.x), d1 = fmaf(0.5f, pq[x].y, A.y),
+                          d2 = fmaf(0.5f, pq[x].z, A.z);
+              const float sq = fmaxf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), 1.0e-30f);
+              const float v = (sq * rsqrtf(sq) - A.w) + B.x;
+              uu[j][x] = v > B.y ? kFarOffset : fmaxf(v, 0.0f);
+            }
+          }
+        }
+        const unsigned bs = bw[j] & 0xffffu;
+        const uint32_t* row = bsrc + int64_t(s) * p.n_t_pad + bs;
+        direct_accumulate<FMT>(acc, uu[j], 1.0e29f, row, unsigned(p.n_t_pad - 1) - bs, mm[j]);
+      }
+    }
+    float* dst = p.part + ((int64_t(tile) * p.n_seg + seg) * SW + sp) * P + px0;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) dst[x * 32] = acc[x];
+  }
+  if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Sum of every pixel over phases (in order) and segments (in order), written
+// to its place in the image; also clears the image outside the mask.  The
+// loads of 8 segments are issued before their sums, so a pixel costs about
+// one L2 round trip per 8 segments.
+template <int P, int SW>
+__global__ void __launch_bounds__(256) direct_reduce_kernel(const __grid_constant__ DirectParams p) {
+  constexpr int K = 8;
+  for (int64_t r = blockIdx.x; r < p.n_zero_runs; r += gridDim.x) {
+    const int st0 = p.zero_runs[2 * r], len = p.zero_runs[2 * r + 1];
+    for (int i2 = threadIdx.x; i2 < len; i2 += blockDim.x) p.out[st0 + i2] = 0.0f;
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int64_t n = int64_t(p.n_tiles) * P;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int o = __ldcg(p.slot + idx);
+    if (o < 0) continue;
+    const int64_t tile = idx / P;
+    const int q = int(idx - tile * P);
+    const float* src = p.part + tile * p.n_seg * SW * P + q;
+    float t = 0.0f;
+    for (int s0 = 0; s0 < p.n_seg; s0 += K) {
+      float x[K][SW];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ph = 0; ph < SW; ++ph)
+          x[k][ph] = s0 + k < p.n_seg ? __ldcg(src + (int64_t(s0 + k) * SW + ph) * P) : 0.0f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (s0 + k >= p.n_seg) break;
+        float v = 0.0f;
+#pragma unroll
+        for (int ph = 0; ph < SW; ++ph) v += x[k][ph];
+        t += v;
+      }
+    }
+    p.out[o] = t;
+  }
+}
+
+template <typename K>
+cudaError_t launch_pdl(K kern, unsigned grid, unsigned threads, const DirectParams& dp, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1u, 1u);
+  cfg.blockDim = dim3(threads, 1u, 1u);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, dp);
+}
+
+template <int P, int SW, int FMT, int DELAYS>
+cudaError_t launch_direct_fmt(const DirectParams& dp, int n_sm, cudaStream_t st) {
+  auto kern = gather_direct_kernel<P, SW, FMT, DELAYS>;
+  const int threads = 32 * (P / 128) * SW;
+  static int per_sm = 0;  // resident CTAs per SM (per instantiation, looked up once)
+  if (per_sm == 0) {
+    int v = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, 0);
+    if (e != cudaSuccess) return e;
+    per_sm = v > 0 ? v : 1;
+  }
+  const int64_t n_units = int64_t(dp.n_tiles) * dp.n_seg;
+  const unsigned grid = unsigned(std::min<int64_t>(n_units, int64_t(per_sm) * n_sm));
+  cudaError_t e = launch_pdl(kern, grid, unsigned(threads), dp, st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = int64_t(dp.n_tiles) * P;
+  const unsigned rgrid = unsigned(std::min<int64_t>((n + 255) / 256, int64_t(n_sm) * 8));
+  return launch_pdl(direct_reduce_kernel<P, SW>, std::max(rgrid, 1u), 256u, dp, st);
+}
+
+template <int P, int SW, int DELAYS>
+cudaError_t launch_direct_t(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
+  if (fmt == kBF32) return launch_direct_fmt<P, SW, kBF32, DELAYS>(dp, n_sm, st);
+  if (fmt == kBBF16P) return launch_direct_fmt<P, SW, kBBF16P, DELAYS>(dp, n_sm, st);
+  if (fmt == kBF16P) return launch_direct_fmt<P, SW, kBF16P, DELAYS>(dp, n_sm, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t direct_part_floats(const GatherConfig& c, int n_tiles, int n_seg) {
+  return size_t(n_tiles) * n_seg * c.SW * c.P;
+}
+
+cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc& d, int n_sm,
+                                 cudaStream_t st) {
+  if (d.n_frames != 1 || c.FB != 1 || d.n_fg != 1 || n_sm < 1 || !d.part) return cudaErrorInvalidValue;
+  DirectParams dp;
+  dp.u = d.u;
+  dp.anchor = d.anchor;
+  dp.pix = d.pix;
+  dp.base = d.base;
+  dp.slot = d.slot;
+  dp.zero_runs = d.zero_runs;
+  dp.b = d.b;
+  dp.m = d.m;
+  dp.out = d.out;
+  dp.part = d.part;
+  dp.n_zero_runs = d.n_zero_runs;
+  dp.n_sensors = d.n_sensors;
+  dp.n_sensors_pad = d.n_sensors_pad;
+  dp.n_t_pad = d.n_t_pad;
+  dp.n_tiles = d.n_tiles;
+  dp.n_seg = d.n_seg;
+  dp.G = d.G;
+  if (c.P == 128 && c.SW == 4)
+    return c.delays ? launch_direct_t<128, 4, 1>(fmt, dp, n_sm, st)
+                    : launch_direct_t<128, 4, 0>(fmt, dp, n_sm, st);
+  if (c.P == 256 && c.SW == 2)
+    return c.delays ? launch_direct_t<256, 2, 1>(fmt, dp, n_sm, st)
+                    : launch_direct_t<256, 2, 0>(fmt, dp, n_sm, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace patbp

@@ -31,6 +31,7 @@ struct pat_bp_s {
   int device = 0;
   int n_sm = 0;
   int max_smem = 232448;              // opt-in shared memory per block (bytes)
+  int max_smem_sm = 233472;           // shared memory per multiprocessor (bytes)
   patbp::GridDesc g;
   int ns = 0, ns_pad = 0, nt = 0, nt_pad = 0;
   double dt = 0.0;

@@ -288,6 +288,10 @@ cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p,
   for (int i = 0; i < p.n_inst; ++i)
     if (p.inst[i].G % p.S || p.inst[i].G > kMaxG || p.inst[i].Wst > p.Wst) return cudaErrorInvalidValue;
   if (p.n_units == 0) return cudaSuccess;
+  if (c.direct) {
+    if (p.n_inst != 1) return cudaErrorInvalidValue;
+    return launch_gather_direct(c, fmt, p.inst[0], c.n_sm, st);
+  }
   return gather_dispatch(c, fmt, p, grid, st, nullptr, 0);
 }
 

@@ -82,6 +82,8 @@ struct GatherConfig {
   int S = 16;       // sensors per stage
   int stages = 4;
   int delays = 0;   // 0 stored table, 1 constant speed computed in the kernel
+  int direct = 0;   // 1: single frame through the unstaged kernels (gather_direct.cu)
+  int n_sm = 0;     // multiprocessors of the device (sizes the unstaged grid)
 };
 
 size_t gather_smem_bytes(const GatherConfig& c, int Wst);
@@ -96,5 +98,12 @@ const void* preprocess_multi_func(int dtype, int fmt, int FB);
 cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
                           cudaStream_t st);
 cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t st);
+// One frame of one instance through the unstaged gather and its reduction
+// kernel (c.FB == 1; d.part holds direct_part_floats floats); same arithmetic
+// and summation order as the staged kernel with one frame per unit.
+cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc& d, int n_sm,
+                                 cudaStream_t st);
+// Phase sums the unstaged gather stores (floats).
+size_t direct_part_floats(const GatherConfig& c, int n_tiles, int n_seg);
 
 }  // namespace patbp

@@ -83,7 +83,7 @@ extern "C" pat_status pat_bp_reconstruct_noalloc(pat_bp_t h, const void* signals
   const size_t sched_bytes = 256;
   const size_t cnt_bytes = align256(n_fg * h->n_tiles * sizeof(int));
   const size_t part_bytes =
-      h->n_seg > 1 ? align256(n_fg * h->n_tiles * h->n_seg * FB * h->P * sizeof(float)) : 0;
+      align256(n_fg * h->n_tiles * h->n_seg * std::max(FB, h->SW) * h->P * sizeof(float));
   const size_t m_bytes = align256(n_fg * h->ns_pad * FB * sizeof(float));
   const size_t b_bytes = align256((n_fg * h->ns * h->nt_pad + kTailRows) * FB * 4);
   const size_t need = sched_bytes + cnt_bytes + part_bytes + m_bytes + b_bytes;
@@ -96,7 +96,7 @@ extern "C" pat_status pat_bp_reconstruct_noalloc(pat_bp_t h, const void* signals
   if (st != PAT_OK) return st;
   unsigned* sched = reinterpret_cast<unsigned*>(base);
   int* counter = reinterpret_cast<int*>(base + sched_bytes);
-  float* part = part_bytes ? reinterpret_cast<float*>(base + sched_bytes + cnt_bytes) : nullptr;
+  float* part = reinterpret_cast<float*>(base + sched_bytes + cnt_bytes);
   float* m = reinterpret_cast<float*>(base + sched_bytes + cnt_bytes + part_bytes);
   void* b = base + sched_bytes + cnt_bytes + part_bytes + m_bytes;
   // what must start at zero: the unit tickets and the segment counters

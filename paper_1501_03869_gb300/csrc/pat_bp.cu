@@ -136,6 +136,7 @@ static pat_status new_handle(const GridDesc& g, int n_sensors, int n_samples, do
   }
   h->n_sm = prop.multiProcessorCount;
   h->max_smem = int(prop.sharedMemPerBlockOptin);
+  h->max_smem_sm = int(prop.sharedMemPerMultiprocessor);
   h->g = g;
   h->ns = n_sensors;
   h->ns_pad = round_up(n_sensors, 4);
@@ -318,8 +319,10 @@ pat_status ensure_buffers_fb(pat_bp_t h, int n_frames, int FB) {
   const size_t m_need = n_fg * h->ns_pad * FB * sizeof(float);
   if ((st = grow_zeroed(reinterpret_cast<void**>(&h->d_m), &h->m_cap, m_need, "multipliers")) != PAT_OK)
     return st;
-  if (h->n_seg > 1) {
-    const size_t part_need = n_fg * h->n_tiles * h->n_seg * FB * h->P * sizeof(float);
+  {
+    // segment partials of the staged kernel, or one frame's phase sums
+    const size_t part_need =
+        n_fg * h->n_tiles * h->n_seg * std::max(FB, h->SW) * h->P * sizeof(float);
     if ((st = grow_zeroed(reinterpret_cast<void**>(&h->d_part), &h->part_cap, part_need,
                           "segment partials")) != PAT_OK)
       return st;
@@ -356,6 +359,7 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
   c.P = h->P;
   c.SW = h->SW;
   c.delays = h->delays;
+  c.n_sm = h->n_sm;
   c.FB = FB;
   c.S = S;
   c.stages = 6;
@@ -375,6 +379,13 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
 // frames share a unit.  No choice here changes the summation order.
 GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst) {
   const size_t limit = size_t(h->max_smem);
+  if (n_frames == 1 && !(h->flags & PAT_FLAG_STAGED_SINGLE)) {
+    // one frame: the unstaged kernels (same arithmetic and order as the
+    // staged kernel with one frame per unit)
+    GatherConfig c = config_for(h, 1, 16, 72 * 1024, wst);
+    c.direct = 1;
+    return c;
+  }
   for (int FB = frames_per_group(n_frames); FB >= 1; FB /= 2) {
     const int fi = fb_index(FB);
     GatherConfig c;

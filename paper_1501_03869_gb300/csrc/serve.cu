@@ -106,7 +106,7 @@ size_t resident_total(pat_srv_t s) {
 size_t subject_need(pat_srv_t s, pat_bp_t h) {
   const size_t frames = size_t(s->cfg.max_batch_frames);
   size_t work = (frames * h->ns * h->nt_pad + 16 * 8) * 4 + frames * h->ns_pad * 4;
-  if (h->n_seg > 1) work += frames * h->n_tiles * h->n_seg * h->P * 4 + frames * h->n_tiles * 4;
+  work += std::max(frames, size_t(h->SW)) * h->n_tiles * h->n_seg * h->P * 4 + frames * h->n_tiles * 4;
   return table_device_bytes(h) + work;
 }
 

@@ -317,3 +317,20 @@ def test_fast_marching_beats_constant_speed_on_the_gpu():
     ref = np.zeros(w.speed.size)
     ref[pix] = oracle.bp(T, p, w.dt)
     assert rel_l2(img_fmm, ref.reshape(w.speed.shape)) <= FP32_REL_L2
+
+
+def test_first_frame_after_device_memory_reuse():
+    """Kernels that start before the previous kernel has finished must not
+    read lines an earlier kernel left in L1: a handle whose buffers reuse the
+    device memory of a closed handle gives, on its very first frame, the same
+    bits through the unstaged and the staged gather."""
+    w0 = synth.config5_subject(4, n_frames=1, n_sensors=512, shape=(24, 40, 40), nt=600)
+    for fl in (0, _lib.PAT_FLAG_STAGED_SINGLE):
+        with const_handle(w0, 1500.0, flags=fl) as bp:
+            run(bp, w0.signals)
+    w = synth.config5_subject(4, n_frames=1, n_sensors=1024)
+    with const_handle(w, 1500.0) as a:
+        first = run(a, w.signals)
+    with const_handle(w, 1500.0, flags=_lib.PAT_FLAG_STAGED_SINGLE) as b:
+        ref = run(b, w.signals)
+    assert np.array_equal(first, ref)

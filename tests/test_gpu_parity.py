@@ -249,3 +249,36 @@ def test_config5_full_grid_sensor_subset(dtype):
         assert_fp32_parity(got, ref, np.abs(w.p0).max())
     else:
         assert rel_l2(got[0], ref[0]) <= LOWP_REL_L2
+
+
+@pytest.mark.parametrize("tile_flag", [0, _lib.PAT_FLAG_TILE_256])
+def test_single_frame_unstaged_equals_staged_bitwise(tile_flag):
+    """One frame goes through the unstaged gather by default; forcing the
+    staged (TMA pipeline) kernel must give the same bits, for every signal
+    dtype and both delay sources, with 8 sensor segments per tile."""
+    w = synth.config2(n_frames=1, n_lines=3)
+    sig = w.signals[:1]
+    makers = {
+        "table": lambda f: BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+                              flags=f | tile_flag),
+        "constant": lambda f: BP.constant(1560.0, w.speed.shape, w.dx, w.origin, w.sensors, w.dt,
+                                          w.nt, mask=w.mask, flags=f | tile_flag),
+    }
+    for kind, make in makers.items():
+        with make(0) as a, make(_lib.PAT_FLAG_STAGED_SINGLE) as b:
+            assert a.info["split"] == 8
+            for dtype in ("f32", "bf16", "f16"):
+                if dtype == "f32":
+                    s = torch.from_numpy(np.ascontiguousarray(sig)).cuda()
+                    sc = None
+                else:
+                    codes, scl, _ = synth.quantise(sig, dtype)
+                    tdt = torch.bfloat16 if dtype == "bf16" else torch.float16
+                    s = torch.from_numpy(codes.astype(np.int16)).cuda().view(tdt)
+                    sc = torch.from_numpy(scl).cuda()
+                ra = a.reconstruct(s, scales=sc).cpu().numpy()
+                rb = b.reconstruct(s, scales=sc).cpu().numpy()
+                a.sync()
+                b.sync()
+                assert np.array_equal(ra, rb), (kind, dtype)
+                assert np.isfinite(ra).all()
