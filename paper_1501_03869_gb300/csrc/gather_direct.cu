@@ -102,14 +102,15 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
   const int pg = warp % PW, sp = warp / PW;
   const int px0 = pg * 128 + lane;
   const int64_t n_units = int64_t(p.n_tiles) * p.n_seg;
-  if (threadIdx.x == 0) {
+  if (DELAYS != 0 && threadIdx.x == 0) {
     prefetch_unit<P, DELAYS>(p, blockIdx.x, n_units);
     prefetch_unit<P, DELAYS>(p, int64_t(blockIdx.x) + gridDim.x, n_units);
   }
   const uint32_t* bsrc = static_cast<const uint32_t*>(p.b);
   bool waited = false;
   for (int64_t unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
-    if (threadIdx.x == 0) prefetch_unit<P, DELAYS>(p, unit + 2 * int64_t(gridDim.x), n_units);
+    if (DELAYS != 0 && threadIdx.x == 0)
+      prefetch_unit<P, DELAYS>(p, unit + 2 * int64_t(gridDim.x), n_units);
     const int tile = int(unit / p.n_seg);
     const int seg = int(unit - int64_t(tile) * p.n_seg);
     const int s_lo = seg * p.G, s_hi = min(p.n_sensors, s_lo + p.G);
@@ -119,70 +120,98 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
       for (int x = 0; x < 4; ++x) pq[x] = __ldcg(p.pix + int64_t(tile) * P + px0 + x * 32);
     }
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    // Sensors of this phase in chunks of CH: the loads that do not depend on
-    // the preprocessing (delay data, window bases) are issued for the chunk
-    // first -- for the first chunk before waiting for the preprocessing grid.
-    for (int c0 = s_lo + sp; c0 < s_hi; c0 += CH * SW) {
-      uint32_t bw[CH];
-      float uu[CH][4];
-      float4 an[DELAYS ? CH : 1][2];
+    if constexpr (DELAYS == 0) {
+      // Table offsets: one sensor at a time, software-pipelined -- the next
+      // sensor's offsets and window base are in flight while this one
+      // gathers (the first ones before waiting for the preprocessing grid).
+      float un[4];
+      uint32_t bn = 0u;
+      auto load_next = [&](int s) {
+        bn = uint32_t(__ldcg(p.base + int64_t(tile) * p.n_sensors_pad + s));
+        const float* urow = p.u + (int64_t(tile) * p.n_sensors + s) * P + px0;
 #pragma unroll
-      for (int j = 0; j < CH; ++j) {
-        const int s = c0 + j * SW;
-        const bool ok = s < s_hi;
-        bw[j] = ok ? uint32_t(__ldcg(p.base + int64_t(tile) * p.n_sensors_pad + s)) : 0u;
-        if constexpr (DELAYS == 0) {
-          const float* urow = p.u + (int64_t(tile) * p.n_sensors + s) * P + px0;
-#pragma unroll
-          for (int x = 0; x < 4; ++x) uu[j][x] = ok ? __ldcg(urow + x * 32) : kFarOffset;
-        } else {
-          const float4* ap = reinterpret_cast<const float4*>(p.anchor) +
-                             (int64_t(tile) * p.n_sensors_pad + (ok ? s : s_lo)) * 2;
-          an[j][0] = __ldcg(ap);
-          an[j][1] = __ldcg(ap + 1);
-          if (!ok) an[j][1].y = -1.0f;  // cap below every offset: nothing to add
+        for (int x = 0; x < 4; ++x) un[x] = __ldcg(urow + x * 32);
+      };
+      if (s_lo + sp < s_hi) load_next(s_lo + sp);
+      for (int s = s_lo + sp; s < s_hi; s += SW) {
+        const float uu[4] = {un[0], un[1], un[2], un[3]};
+        const unsigned bs = bn & 0xffffu;
+        if (s + SW < s_hi) load_next(s + SW);
+        if (!waited) {
+          // integrand and multipliers come from the preprocessing grid
+          asm volatile("griddepcontrol.wait;" ::: "memory");
+          waited = true;
         }
+        const float mm = __ldcg(p.m + s);
+        const uint32_t* row = bsrc + int64_t(s) * p.n_t_pad + bs;
+        direct_accumulate<FMT>(acc, uu, 1.0e29f, row, unsigned(p.n_t_pad - 1) - bs, mm);
       }
-      if (!waited) {
-        // integrand and multipliers come from the preprocessing grid
-        asm volatile("griddepcontrol.wait;" ::: "memory");
-        waited = true;
-      }
-      float mm[CH];
-#pragma unroll
-      for (int j = 0; j < CH; ++j) mm[j] = c0 + j * SW < s_hi ? __ldcg(p.m + c0 + j * SW) : 0.0f;
-#pragma unroll
-      for (int j = 0; j < CH; ++j) {
-        const int s = min(c0 + j * SW, s_hi - 1);
-        if constexpr (DELAYS != 0) {
-          const float4 A = an[j][0], B = an[j][1];
-          if (B.w == 0.0f) {
-            const float m2u0 = -2.0f * A.w;
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-              const float num =
-                  fmaf(pq[x].x, A.x, fmaf(pq[x].y, A.y, fmaf(pq[x].z, A.z, pq[x].w)));
-              const float sq = num + B.z;
-              const float y = rsqrtf(sq);
-              const float da = sq * y - A.w;
-              const float r = fmaf(-da, da, fmaf(m2u0, da, num));
-              const float v = fmaf(r, 0.5f * y, da) + B.x;
-              uu[j][x] = v > B.y ? kFarOffset : fmaxf(v, 0.0f);
-            }
+    } else {
+      // Sensors of this phase in chunks of CH: the loads that do not depend on
+      // the preprocessing (delay data, window bases) are issued for the chunk
+      // first -- for the first chunk before waiting for the preprocessing grid.
+      for (int c0 = s_lo + sp; c0 < s_hi; c0 += CH * SW) {
+        uint32_t bw[CH];
+        float uu[CH][4];
+        float4 an[DELAYS ? CH : 1][2];
+  #pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int s = c0 + j * SW;
+          const bool ok = s < s_hi;
+          bw[j] = ok ? uint32_t(__ldcg(p.base + int64_t(tile) * p.n_sensors_pad + s)) : 0u;
+          if constexpr (DELAYS == 0) {
+            const float* urow = p.u + (int64_t(tile) * p.n_sensors + s) * P + px0;
+  #pragma unroll
+            for (int x = 0; x < 4; ++x) uu[j][x] = ok ? __ldcg(urow + x * 32) : kFarOffset;
           } else {
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-              const float d0 = fmaf(0.5f, pq[x].x, A.x), d1 = fmaf(0.5f, pq[x].y, A.y),
-                          d2 = fmaf(0.5f, pq[x].z, A.z);
-              const float sq = fmaxf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), 1.0e-30f);
-              const float v = (sq * rsqrtf(sq) - A.w) + B.x;
-              uu[j][x] = v > B.y ? kFarOffset : fmaxf(v, 0.0f);
-            }
+            const float4* ap = reinterpret_cast<const float4*>(p.anchor) +
+                               (int64_t(tile) * p.n_sensors_pad + (ok ? s : s_lo)) * 2;
+            an[j][0] = __ldcg(ap);
+            an[j][1] = __ldcg(ap + 1);
+            if (!ok) an[j][1].y = -1.0f;  // cap below every offset: nothing to add
           }
         }
-        const unsigned bs = bw[j] & 0xffffu;
-        const uint32_t* row = bsrc + int64_t(s) * p.n_t_pad + bs;
-        direct_accumulate<FMT>(acc, uu[j], 1.0e29f, row, unsigned(p.n_t_pad - 1) - bs, mm[j]);
+        if (!waited) {
+          // integrand and multipliers come from the preprocessing grid
+          asm volatile("griddepcontrol.wait;" ::: "memory");
+          waited = true;
+        }
+        float mm[CH];
+  #pragma unroll
+        for (int j = 0; j < CH; ++j) mm[j] = c0 + j * SW < s_hi ? __ldcg(p.m + c0 + j * SW) : 0.0f;
+  #pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int s = min(c0 + j * SW, s_hi - 1);
+          if constexpr (DELAYS != 0) {
+            const float4 A = an[j][0], B = an[j][1];
+            if (B.w == 0.0f) {
+              const float m2u0 = -2.0f * A.w;
+  #pragma unroll
+              for (int x = 0; x < 4; ++x) {
+                const float num =
+                    fmaf(pq[x].x, A.x, fmaf(pq[x].y, A.y, fmaf(pq[x].z, A.z, pq[x].w)));
+                const float sq = num + B.z;
+                const float y = rsqrtf(sq);
+                const float da = sq * y - A.w;
+                const float r = fmaf(-da, da, fmaf(m2u0, da, num));
+                const float v = fmaf(r, 0.5f * y, da) + B.x;
+                uu[j][x] = v > B.y ? kFarOffset : fmaxf(v, 0.0f);
+              }
+            } else {
+  #pragma unroll
+              for (int x = 0; x < 4; ++x) {
+                const float d0 = fmaf(0.5f, pq[x].x, A.x), d1 = fmaf(0.5f, pq[x].y, A.y),
+                            d2 = fmaf(0.5f, pq[x].z, A.z);
+                const float sq = fmaxf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), 1.0e-30f);
+                const float v = (sq * rsqrtf(sq) - A.w) + B.x;
+                uu[j][x] = v > B.y ? kFarOffset : fmaxf(v, 0.0f);
+              }
+            }
+          }
+          const unsigned bs = bw[j] & 0xffffu;
+          const uint32_t* row = bsrc + int64_t(s) * p.n_t_pad + bs;
+          direct_accumulate<FMT>(acc, uu[j], 1.0e29f, row, unsigned(p.n_t_pad - 1) - bs, mm[j]);
+        }
       }
     }
     float* dst = p.part + ((int64_t(tile) * p.n_seg + seg) * SW + sp) * P + px0;
