@@ -29,19 +29,6 @@ __device__ __forceinline__ float load_sample(const void* sig, int64_t i) {
   }
 }
 
-// b_k of one pressure row (zero past the record): 2 p_k - 2 t_k dp/dt with
-// t_k / dt = k, central difference inside, one-sided at both ends.
-template <int DT>
-__device__ __forceinline__ float integrand(const void* sig, int64_t row0, float sc, int k, int n) {
-  if (k >= n) return 0.0f;
-  const float pk = load_sample<DT>(sig, row0 + k) * sc;
-  if (k == 0) return 2.0f * pk;
-  const float pm = load_sample<DT>(sig, row0 + k - 1) * sc;
-  if (k == n - 1) return fmaf(-2.0f * float(k), pk - pm, 2.0f * pk);
-  const float pp = load_sample<DT>(sig, row0 + k + 1) * sc;
-  return fmaf(-float(k), pp - pm, 2.0f * pk);
-}
-
 template <int FMT>
 __device__ __forceinline__ uint32_t encode_pair(float v0, float v1) {
   if constexpr (FMT == kBBF16P) {
@@ -87,13 +74,15 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
     row0[fb] = r * n;
     sc[fb] = p.scales ? p.scales[r] : 1.0f;
   }
-  // b_{k0..k0+K} of frame fb (K + 1 values; the last feeds the pair slope)
+  // b_{k0..k0+K} of frame fb (K + 1 values; the last feeds the pair slope).
+  // Products and differences are explicitly rounded (no contraction into
+  // FMAs): the values do not depend on how the compiler schedules them.
   auto b_run = [&](int fb, int k0, float (&b)[K + 1]) {
     float v[K + 3];  // p_{k0-1} .. p_{k0+K+1}
 #pragma unroll
     for (int j = 0; j < K + 3; ++j) {
       const int k = k0 - 1 + j;
-      v[j] = (k >= 0 && k < n) ? load_sample<DT>(p.sig, row0[fb] + k) * sc[fb] : 0.0f;
+      v[j] = (k >= 0 && k < n) ? __fmul_rn(load_sample<DT>(p.sig, row0[fb] + k), sc[fb]) : 0.0f;
     }
 #pragma unroll
     for (int j = 0; j <= K; ++j) {
@@ -101,8 +90,8 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
       float r;
       if (k >= n) r = 0.0f;
       else if (k == 0) r = 2.0f * v[j + 1];
-      else if (k == n - 1) r = fmaf(-2.0f * float(k), v[j + 1] - v[j], 2.0f * v[j + 1]);
-      else r = fmaf(-float(k), v[j + 2] - v[j], 2.0f * v[j + 1]);
+      else if (k == n - 1) r = fmaf(-2.0f * float(k), __fsub_rn(v[j + 1], v[j]), 2.0f * v[j + 1]);
+      else r = fmaf(-float(k), __fsub_rn(v[j + 2], v[j]), 2.0f * v[j + 1]);
       b[j] = r;
     }
   };

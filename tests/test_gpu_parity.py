@@ -282,3 +282,28 @@ def test_single_frame_unstaged_equals_staged_bitwise(tile_flag):
                 b.sync()
                 assert np.array_equal(ra, rb), (kind, dtype)
                 assert np.isfinite(ra).all()
+
+
+def test_single_fp32_frame_host_round_trip_and_split_calls():
+    """One FP32 frame: pat_bp_reconstruct forms the integrand inside the
+    gather; the host round trip (exactly sized staging buffers), the two-call
+    API (preprocessing kernel, then gather) and the staged kernel give the same
+    bits, with and without per-row scales."""
+    w = synth.config2(n_frames=1, n_lines=2)
+    sig = np.ascontiguousarray(w.signals[:1])
+    sc = np.random.default_rng(4).uniform(0.5, 2.0, (1, w.n_sensors)).astype(np.float32)
+    with BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask) as bp, \
+            BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+               flags=_lib.PAT_FLAG_STAGED_SINGLE) as st:
+        s = torch.from_numpy(sig).cuda()
+        for scales in (None, torch.from_numpy(sc).cuda()):
+            a = bp.reconstruct(s, scales=scales).cpu().numpy()
+            bp.preprocess(s, scales=scales)
+            out = torch.empty(bp.out_shape(1), device="cuda")
+            b = bp.gather(1, out).cpu().numpy()
+            c = st.reconstruct(s, scales=scales).cpu().numpy()
+            bp.sync()
+            st.sync()
+            assert np.array_equal(a, b) and np.array_equal(a, c)
+        h = bp.reconstruct_host(sig)
+        assert np.array_equal(h, bp.reconstruct(s).cpu().numpy())
