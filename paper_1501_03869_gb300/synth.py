@@ -159,6 +159,21 @@ def skull_ring_2d(shape, r_in_px, thick_px, rng, r_in_var=0.0, thick_var=0.0,
     return speed.astype(np.float32)
 
 
+def speed_error(speed, rng, frac=0.017, region=None):
+    """The speed-of-sound error of Sec. III's robustness study: uncorrelated
+    Gaussian noise whose mean and standard deviation are both frac times the
+    map's maximum, added independently at every node of `region` (default: the
+    skull, i.e. the nodes whose speed is neither water's nor brain's)."""
+    speed = np.asarray(speed, dtype=np.float64)
+    if region is None:
+        region = (np.abs(speed - C_WATER) > 1e-3) & (np.abs(speed - C_BRAIN) > 1e-3)
+    top = float(speed.max())
+    out = speed.copy()
+    n = int(np.count_nonzero(region))
+    out[region] += rng.normal(frac * top, frac * top, n)
+    return out.astype(np.float32)
+
+
 def nearest_nodes_mask(shape, count):
     """The `count` nodes nearest the grid centre; equal radii ordered by linear index."""
     r = node_radius_px(shape).ravel()

@@ -535,3 +535,28 @@ def test_paper_shaped_workload_matches_printed_numbers():
     # record length covers the end time 1.5 d / c0 of Sec. III
     d = 2 * np.linalg.norm(w.sensors[0, :2])
     assert w.nt * w.dt >= g["end_time_factor"] * d / synth.C_WATER
+
+
+# ------------------------------------------------------ speed-map errors --
+@pytest.mark.parametrize("shape,seed", [((31, 27), 5), ((11, 13, 9), 6)])
+def test_faster_medium_never_arrives_later(shape, seed):
+    """The first-order upwind scheme is monotone: raising the speed at any set
+    of nodes (here the Sec. III error model with its positive mean, clipped
+    at zero) can only make arrivals earlier, at every node."""
+    rng = np.random.default_rng(seed)
+    sp = _heterogeneous(shape, seed)
+    h = 1e-4
+    origin = np.zeros(len(shape))
+    src = np.array([(n - 1) * h * f for n, f in zip(shape[::-1], (0.3, 0.6, 0.4))])
+    region = rng.uniform(0, 1, shape) < 0.5
+    err = synth.speed_error(sp, rng, region=region).astype(np.float64)
+    faster = np.maximum(err, sp)
+    T = oracle.fmm_point(sp, h, origin, src)
+    Tf = oracle.fmm_point(faster, h, origin, src)
+    assert np.all(Tf <= T + 1e-15 * T.max())
+    assert np.any(Tf < T)
+    # and the error model itself: mean and spread 1.7 % of the maximum speed, on the region only
+    d = (err - sp)[region]
+    assert np.all(err[~region] == sp[~region].astype(np.float32))
+    assert abs(d.mean() - 0.017 * sp.max()) < 0.2 * 0.017 * sp.max()
+    assert abs(d.std() - 0.017 * sp.max()) < 0.2 * 0.017 * sp.max()
