@@ -1,5 +1,5 @@
 """Sec. III's robustness study through the GPU path: the skull's speed map
-carries an error (uncorrelated Gaussian noise, mean and spread 1.7 % of the
+carries an error (independent Gaussian noise per node, mean and spread 1.7 % of the
 map's maximum), the table is rebuilt from the wrong map, and the same data are
 reconstructed.  The wrong-map image still localises an absorber near the skull
 as the true-map image does, and stays better than the constant-speed (1560 m/s)
