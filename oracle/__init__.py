@@ -8,8 +8,9 @@ The arithmetic lives in ``oracle.c`` (plain C, double precision); this module
 only compiles it with gcc on first use and marshals numpy arrays:
 
 * :func:`fmm_point`, :func:`fmm_sources` -- Sec. II-B, first-order Godunov fast
-  marching from a point source (corners of the enclosing cell accepted with
-  exact distance times local slowness) or from an arbitrary accepted set.
+  marching (or, with ``order=2``, the printed second-order stencil) from a
+  point source (corners of the enclosing cell accepted with exact distance
+  times local slowness) or from an arbitrary accepted set.
 * :func:`travel_table` -- one fast-marching run per sensor (Sec. II-B: each
   sensor is used as the source since ray paths are reversible), values read
   at the requested pixels.
@@ -60,9 +61,10 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             lib.oracle_fmm_sources.argtypes = [ctypes.c_int, _i64p, ctypes.c_double, _dp,
-                                               _i64p, _dp, ctypes.c_int64, _dp, _i64p, _i64p]
+                                               _i64p, _dp, ctypes.c_int64, _dp, _i64p, _i64p,
+                                               ctypes.c_int]
             lib.oracle_fmm_point.argtypes = [ctypes.c_int, _i64p, ctypes.c_double, _dp, _dp,
-                                             _dp, _dp, _i64p, _i64p]
+                                             _dp, _dp, _i64p, _i64p, ctypes.c_int]
             lib.oracle_preprocess.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, _dp]
             lib.oracle_sample.argtypes = [_dp, ctypes.c_int64, ctypes.c_double]
             lib.oracle_sample.restype = ctypes.c_double
@@ -90,49 +92,51 @@ def _shape_n(shape):
     return np.ascontiguousarray(shape[::-1], dtype=np.int64)
 
 
-def fmm_sources(speed, h, src_idx, src_T, return_order=False):
-    """Fast marching from accepted nodes src_idx (linear indices) with values src_T."""
+def fmm_sources(speed, h, src_idx, src_T, return_order=False, order=1):
+    """Fast marching from accepted nodes src_idx (linear indices) with values src_T;
+    order 1 (first-order upwind) or 2 (the second-order stencil of Sec. II-B)."""
     lib = _load()
     speed = np.ascontiguousarray(speed, dtype=np.float64)
     n = _shape_n(speed.shape)
     src_idx = np.ascontiguousarray(src_idx, dtype=np.int64).ravel()
     src_T = np.ascontiguousarray(src_T, dtype=np.float64).ravel()
     T = np.empty(speed.shape, dtype=np.float64)
-    order = np.empty(speed.size, dtype=np.int64) if return_order else None
+    pops = np.empty(speed.size, dtype=np.int64) if return_order else None
     npop = np.zeros(1, dtype=np.int64)
     rc = lib.oracle_fmm_sources(speed.ndim, _i(n), float(h), _d(speed), _i(src_idx), _d(src_T),
-                                src_idx.size, _d(T), _i(order) if return_order else None, _i(npop))
+                                src_idx.size, _d(T), _i(pops) if return_order else None, _i(npop),
+                                int(order))
     _check(rc, "fmm_sources")
     if return_order:
-        return T, order[: int(npop[0])]
+        return T, pops[: int(npop[0])]
     return T
 
 
-def fmm_point(speed, h, origin, src, return_order=False):
-    """Fast marching from a point source at src (metres, x first)."""
+def fmm_point(speed, h, origin, src, return_order=False, order=1):
+    """Fast marching from a point source at src (metres, x first); order 1 or 2."""
     lib = _load()
     speed = np.ascontiguousarray(speed, dtype=np.float64)
     n = _shape_n(speed.shape)
     origin = np.ascontiguousarray(origin, dtype=np.float64)
     src = np.ascontiguousarray(src, dtype=np.float64)
     T = np.empty(speed.shape, dtype=np.float64)
-    order = np.empty(speed.size, dtype=np.int64) if return_order else None
+    pops = np.empty(speed.size, dtype=np.int64) if return_order else None
     npop = np.zeros(1, dtype=np.int64)
     rc = lib.oracle_fmm_point(speed.ndim, _i(n), float(h), _d(origin), _d(speed), _d(src), _d(T),
-                              _i(order) if return_order else None, _i(npop))
+                              _i(pops) if return_order else None, _i(npop), int(order))
     _check(rc, "fmm_point")
     if return_order:
-        return T, order[: int(npop[0])]
+        return T, pops[: int(npop[0])]
     return T
 
 
-def travel_table(speed, h, origin, sensors, pix):
+def travel_table(speed, h, origin, sensors, pix, order=1):
     """T[s, j]: arrival time from sensor s at pixel linear index pix[j]."""
     sensors = np.asarray(sensors, dtype=np.float64)
     pix = np.asarray(pix, dtype=np.int64)
     out = np.empty((sensors.shape[0], pix.size), dtype=np.float64)
     for s in range(sensors.shape[0]):
-        out[s] = fmm_point(speed, h, origin, sensors[s]).ravel()[pix]
+        out[s] = fmm_point(speed, h, origin, sensors[s], order=order).ravel()[pix]
     return out
 
 
@@ -193,7 +197,7 @@ def bp(T, p, dt, weights=None):
     return out
 
 
-def reconstruct(speed, h, origin, sensors, p, dt, mask=None, weights=None, T=None):
+def reconstruct(speed, h, origin, sensors, p, dt, mask=None, weights=None, T=None, order=1):
     """Whole chain on a grid: fast-marching table, then back projection of each
     frame.  p is [ns, nt] or [F, ns, nt]; the output is dense ([F,] grid shape)
     with zeros outside the mask.  A precomputed table T[ns, npix] may be passed.
@@ -204,7 +208,7 @@ def reconstruct(speed, h, origin, sensors, p, dt, mask=None, weights=None, T=Non
     else:
         pix = np.flatnonzero(np.asarray(mask).ravel())
     if T is None:
-        T = travel_table(speed, h, origin, sensors, pix)
+        T = travel_table(speed, h, origin, sensors, pix, order=order)
     p = np.asarray(p, dtype=np.float64)
     single = p.ndim == 2
     frames = p[None] if single else p

@@ -24,7 +24,9 @@
  *      interpolation in u = t/dt; samples after the last one contribute zero.
  *
  * Readings where the paper is silent (each is listed in the design doc):
- *   - first-order Godunov update rather than the printed second-order stencil;
+ *   - first-order Godunov update by default; the printed second-order stencil
+ *     (order 2) uses the one-sided second-order difference on an axis where
+ *     the two upwind neighbours on the same side are accepted and monotone;
  *   - off-grid point source: the 2^ndim corners of the enclosing cell are
  *     accepted with T = |x - r_s| * f(x), f = 1/c at the node;
  *   - weights w_i default to 1/N_s and the integrand carries the factor 2 of
@@ -182,6 +184,76 @@ static double godunov_update(const grid_t* g, const double* T, const uint8_t* st
   return t;
 }
 
+/* ------------------------------------------- second-order update --- */
+/* Tentative arrival time at node v with the second-order one-sided difference
+ * (3 T_i - 4 T_{i-1} + T_{i-2}) / (2h) of Sec. II-B where it applies.
+ *
+ * Per axis d the upwind side is the one whose accepted neighbour is smaller
+ * (the lower-index side on a tie).  With that neighbour's value t1 and the
+ * value t2 of the node beyond it on the same side: if t2 is accepted and
+ * t2 <= t1 the axis contributes (9/4) (T - (4 t1 - t2)/3)^2, otherwise
+ * (T - t1)^2, as the first-order scheme.  The equation
+ *     sum_d alpha_d (T - a_d)^2 = (h f)^2
+ * is solved by growing the set of contributing axes in increasing a_d: with k
+ * axes, A = sum alpha, B = sum alpha a, C = sum alpha a^2 - (h f)^2 and
+ * T = (B + sqrt(B^2 - A C)) / A; the next axis joins while T exceeds its a.
+ * If including an axis makes B^2 - A C negative, the root without it stays.
+ */
+static double second_order_update(const grid_t* g, const double* T, const uint8_t* state,
+                                  int64_t v, double hf) {
+  int64_t c[3];
+  grid_coords(g, v, c);
+  double a[3], w[3];
+  int na = 0;
+  for (int d = 0; d < g->ndim; ++d) {
+    double t1 = INFINITY;
+    int side = 0;
+    if (c[d] > 0 && state[v - g->stride[d]] == KNOWN) {
+      t1 = T[v - g->stride[d]];
+      side = -1;
+    }
+    if (c[d] + 1 < g->n[d] && state[v + g->stride[d]] == KNOWN && T[v + g->stride[d]] < t1) {
+      t1 = T[v + g->stride[d]];
+      side = 1;
+    }
+    if (side == 0) continue;
+    double alpha = 1.0, ad = t1;
+    int64_t c2 = c[d] + 2 * side;
+    if (c2 >= 0 && c2 < g->n[d]) {
+      int64_t v2 = v + 2 * side * g->stride[d];
+      if (state[v2] == KNOWN && T[v2] <= t1) {
+        alpha = 9.0 / 4.0;
+        ad = (4.0 * t1 - T[v2]) / 3.0;
+      }
+    }
+    a[na] = ad;
+    w[na] = alpha;
+    ++na;
+  }
+  if (na == 0) return INFINITY;
+  /* sort the axes by a ascending (insertion sort, weights follow) */
+  for (int i = 1; i < na; ++i) {
+    double x = a[i], y = w[i];
+    int j = i - 1;
+    while (j >= 0 && a[j] > x) { a[j + 1] = a[j]; w[j + 1] = w[j]; --j; }
+    a[j + 1] = x;
+    w[j + 1] = y;
+  }
+  double A = w[0], B = w[0] * a[0], C = w[0] * a[0] * a[0] - hf * hf;
+  double t = (B + sqrt(B * B - A * C)) / A; /* = a0 + hf / sqrt(alpha0) */
+  for (int k = 1; k < na; ++k) {
+    if (!(t > a[k])) break;
+    double A2 = A + w[k], B2 = B + w[k] * a[k], C2 = C + w[k] * a[k] * a[k];
+    double disc = B2 * B2 - A2 * C2;
+    if (disc < 0.0) break;
+    A = A2;
+    B = B2;
+    C = C2;
+    t = (B + sqrt(disc)) / A;
+  }
+  return t;
+}
+
 /* ------------------------------------------------------ fast marching --- */
 /* Fast marching from an arbitrary accepted initial set.
  *
@@ -194,10 +266,10 @@ static double godunov_update(const grid_t* g, const double* T, const uint8_t* st
  */
 int oracle_fmm_sources(int ndim, const int64_t* n, double h, const double* speed,
                        const int64_t* src_idx, const double* src_T, int64_t n_src,
-                       double* T, int64_t* pop_order, int64_t* n_popped) {
+                       double* T, int64_t* pop_order, int64_t* n_popped, int order) {
   grid_t g;
   if (grid_init(&g, ndim, n) != ORACLE_OK || !(h > 0) || !speed || !T) return ORACLE_ERR_ARG;
-  if (n_src < 1 || !src_idx || !src_T) return ORACLE_ERR_ARG;
+  if (n_src < 1 || !src_idx || !src_T || (order != 1 && order != 2)) return ORACLE_ERR_ARG;
   for (int64_t i = 0; i < g.total; ++i)
     if (!(speed[i] > 0)) return ORACLE_ERR_ARG;
 
@@ -225,7 +297,8 @@ int oracle_fmm_sources(int ndim, const int64_t* n, double h, const double* speed
         if (cc < 0 || cc >= g.n[d]) continue;
         int64_t w = v + side * g.stride[d];
         if (state[w] == KNOWN) continue;
-        double t = godunov_update(&g, T, state, w, h / speed[w]);
+        double t = order == 2 ? second_order_update(&g, T, state, w, h / speed[w])
+                              : godunov_update(&g, T, state, w, h / speed[w]);
         if (t < T[w]) {
           T[w] = t;
           state[w] = TRIAL;
@@ -252,7 +325,8 @@ int oracle_fmm_sources(int ndim, const int64_t* n, double h, const double* speed
         if (cc < 0 || cc >= g.n[d]) continue;
         int64_t w = v + side * g.stride[d];
         if (state[w] == KNOWN) continue;
-        double t = godunov_update(&g, T, state, w, h / speed[w]);
+        double t = order == 2 ? second_order_update(&g, T, state, w, h / speed[w])
+                              : godunov_update(&g, T, state, w, h / speed[w]);
         if (t < T[w]) {
           T[w] = t;
           state[w] = TRIAL;
@@ -274,7 +348,7 @@ done:
  * distance times the local slowness, then fast marching runs from them. */
 int oracle_fmm_point(int ndim, const int64_t* n, double h, const double* origin,
                      const double* speed, const double* src, double* T,
-                     int64_t* pop_order, int64_t* n_popped) {
+                     int64_t* pop_order, int64_t* n_popped, int order) {
   grid_t g;
   if (grid_init(&g, ndim, n) != ORACLE_OK || !(h > 0) || !origin || !src) return ORACLE_ERR_ARG;
   int64_t cell[3] = {0, 0, 0};
@@ -301,7 +375,7 @@ int oracle_fmm_point(int ndim, const int64_t* n, double h, const double* origin,
     idx[m] = v;
     t0[m] = sqrt(dist2) / speed[v];
   }
-  return oracle_fmm_sources(ndim, n, h, speed, idx, t0, ncorner, T, pop_order, n_popped);
+  return oracle_fmm_sources(ndim, n, h, speed, idx, t0, ncorner, T, pop_order, n_popped, order);
 }
 
 /* ------------------------------------------------------ preprocessing --- */

@@ -14,9 +14,9 @@ _pool = None
 
 
 def _chunk_table(args):
-    speed, dx, origin, sensors, pix = args
+    speed, dx, origin, sensors, pix, order = args
     import oracle
-    return oracle.travel_table(speed, dx, origin, sensors, pix)
+    return oracle.travel_table(speed, dx, origin, sensors, pix, order=order)
 
 
 def pool():
@@ -27,8 +27,9 @@ def pool():
     return _pool
 
 
-def travel_table(key, speed, dx, origin, sensors, pix):
-    """T[ns, npix] from the oracle, split over sensors in the pool."""
+def travel_table(key, speed, dx, origin, sensors, pix, order=1):
+    """T[ns, npix] from the oracle (fast-marching order 1 or 2), split over
+    sensors in the pool."""
     if key in _cache:
         return _cache[key]
     sensors = np.asarray(sensors, dtype=np.float64)
@@ -36,7 +37,7 @@ def travel_table(key, speed, dx, origin, sensors, pix):
     k = max(1, min(n, 4 * (os.cpu_count() or 2)))
     bounds = np.linspace(0, n, k + 1).astype(int)
     jobs = [(np.asarray(speed, dtype=np.float64), dx, np.asarray(origin), sensors[a:b],
-             np.asarray(pix)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+             np.asarray(pix), int(order)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
     parts = list(pool().map(_chunk_table, jobs))
     T = np.concatenate(parts, axis=0)
     _cache[key] = T

@@ -560,3 +560,60 @@ def test_faster_medium_never_arrives_later(shape, seed):
     assert np.all(err[~region] == sp[~region].astype(np.float32))
     assert abs(d.mean() - 0.017 * sp.max()) < 0.2 * 0.017 * sp.max()
     assert abs(d.std() - 0.017 * sp.max()) < 0.2 * 0.017 * sp.max()
+
+
+# ------------------------------------------------- second-order stencil --
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_second_order_reproduces_an_oblique_plane_wave_exactly(ndim):
+    """Both one-sided differences are exact for a linear arrival time, so with
+    two exact layers accepted along every low face both orders reproduce an
+    oblique plane wave to rounding (a wrong second-order weight or offset
+    would not)."""
+    n = 24 if ndim == 2 else 12
+    shape = (n,) * ndim
+    c, h = 1500.0, 1e-4
+    k = np.array([0.8, 0.45, 0.39][:ndim])
+    k = k / np.linalg.norm(k)
+    idx = np.indices(shape)[::-1]  # x first
+    T_exact = sum(k[d] * idx[d] * h for d in range(ndim)) / c
+    src = np.flatnonzero(np.any(np.stack([idx[d] < 2 for d in range(ndim)]), axis=0).ravel())
+    sp = np.full(shape, c)
+    for order in (1, 2):
+        T = oracle.fmm_sources(sp, h, src, T_exact.ravel()[src], order=order)
+        assert np.abs(T - T_exact).max() <= 1e-10 * h / c
+
+
+@pytest.mark.parametrize("ndim,sizes,min_ratio2", [(2, (41, 81, 161), 3.5), (3, (21, 41), 2.8)])
+def test_second_order_converges_at_second_order(ndim, sizes, min_ratio2):
+    """A circular (spherical) front accepted exactly inside 0.3 L of the
+    source and marched outward: the order-1 error halves and the order-2 error
+    falls about fourfold each time dx halves (observed orders 1 and 2)."""
+    c, L = 1500.0, 1e-3
+    src = np.array([0.13e-4, -0.07e-4, 0.05e-4])[:ndim]
+    errs = {1: [], 2: []}
+    for n in sizes:
+        h = 2 * L / (n - 1)
+        origin = np.full(ndim, -L)
+        axes = [origin[d] + h * np.arange(n) for d in range(ndim)]
+        mesh = np.meshgrid(*axes[::-1], indexing="ij")
+        dist = np.sqrt(sum((mesh[ndim - 1 - d] - src[d]) ** 2 for d in range(ndim)))
+        sp = np.full((n,) * ndim, c)
+        init = np.flatnonzero((dist < 0.3 * L).ravel())
+        for order in (1, 2):
+            T = oracle.fmm_sources(sp, h, init, (dist / c).ravel()[init], order=order)
+            errs[order].append(np.abs(T - dist / c)[dist >= 0.3 * L].max())
+    for i in range(len(sizes) - 1):
+        assert 1.8 < errs[1][i] / errs[1][i + 1] < 2.3
+        assert errs[2][i] / errs[2][i + 1] > min_ratio2 or i < len(sizes) - 2
+        assert errs[2][i] < 0.25 * errs[1][i]
+
+
+def test_second_order_accept_order_and_causality():
+    """P4 for the second-order march on a heterogeneous grid."""
+    sp = _heterogeneous((29, 23), 3)
+    h = 1e-4
+    T, order = oracle.fmm_point(sp, h, np.zeros(2), np.array([7.3e-4, 9.1e-4]), return_order=True,
+                                order=2)
+    popped = T.ravel()[order]
+    assert np.all(np.diff(popped) >= -1e-15 * popped.max())
+    assert np.isfinite(T).all()
