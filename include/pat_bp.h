@@ -63,6 +63,11 @@ typedef void* pat_stream_t; /* a cudaStream_t; NULL = legacy default stream */
 #define PAT_FLAG_TILE_256 0x20u   /* force 256 pixels per tile                   */
 #define PAT_FLAG_HOST_MIRROR 0x100u /* keep a pinned host copy of the table so the
                                        device copy can be evicted and restored    */
+#define PAT_FLAG_FMM_SECOND_ORDER 0x400u /* build the table with the printed
+                                            second-order stencil of Sec. II-B
+                                            (one-sided difference (3T_i - 4T_{i-1}
+                                            + T_{i-2}) / 2h where the two upwind
+                                            nodes are accepted and monotone)     */
 #define PAT_FLAG_STAGED_SINGLE 0x200u /* single frames through the staged (TMA
                                          pipeline) gather too; by default one
                                          frame takes the unstaged kernel, which
@@ -215,9 +220,10 @@ pat_status pat_bp_restore(pat_bp_t h, pat_stream_t stream);
 pat_status pat_bp_destroy(pat_bp_t h);
 
 /* pat_fmm_host -- the library's own host fast marching (Sec. II-B) from one
- * point source; T_out [grid] receives FP64 arrival times (s).  CPU only. */
+ * point source; order 1 (first-order upwind) or 2 (the printed second-order
+ * stencil); T_out [grid] receives FP64 arrival times (s).  CPU only. */
 pat_status pat_fmm_host(const float* speed_host, const pat_grid* grid, const double* src_xyz,
-                        double* T_out);
+                        int order, double* T_out);
 
 /* pat_table_host -- the table pat_bp_create would upload, built on the host
  * only (no GPU needed): same arguments as pat_bp_create.  info receives the

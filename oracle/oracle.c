@@ -23,7 +23,7 @@
  *      t_ij the travel time from sensor i to pixel j; b is sampled by linear
  *      interpolation in u = t/dt; samples after the last one contribute zero.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - first-order Godunov update by default; the printed second-order stencil
  *     (order 2) uses the one-sided second-order difference on an axis where
  *     the two upwind neighbours on the same side are accepted and monotone;
@@ -198,6 +198,10 @@ static double godunov_update(const grid_t* g, const double* T, const uint8_t* st
  * axes, A = sum alpha, B = sum alpha a, C = sum alpha a^2 - (h f)^2 and
  * T = (B + sqrt(B^2 - A C)) / A; the next axis joins while T exceeds its a.
  * If including an axis makes B^2 - A C negative, the root without it stays.
+ * Unlike the first-order update, the result can depend on exact ties (the
+ * switch t2 <= t1 flips on the last bit): a point source at a cell centre
+ * gives exactly tied neighbours, and two evaluations that differ in rounding
+ * can take different branches there.
  */
 static double second_order_update(const grid_t* g, const double* T, const uint8_t* state,
                                   int64_t v, double hf) {
@@ -240,7 +244,7 @@ static double second_order_update(const grid_t* g, const double* T, const uint8_
     w[j + 1] = y;
   }
   double A = w[0], B = w[0] * a[0], C = w[0] * a[0] * a[0] - hf * hf;
-  double t = (B + sqrt(B * B - A * C)) / A; /* = a0 + hf / sqrt(alpha0) */
+  double t = a[0] + hf / sqrt(w[0]); /* one axis: alpha0 (T - a0)^2 = (h f)^2 */
   for (int k = 1; k < na; ++k) {
     if (!(t > a[k])) break;
     double A2 = A + w[k], B2 = B + w[k] * a[k], C2 = C + w[k] * a[k] * a[k];

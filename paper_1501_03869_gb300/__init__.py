@@ -422,15 +422,16 @@ def reconstruct_multi(bps, signals, outs, scales=None, stream=None):
     return outs
 
 
-def fmm_host(speed, dx, origin, src):
-    """The library's host fast marching (FP64) from one point source."""
+def fmm_host(speed, dx, origin, src, order=1):
+    """The library's host fast marching (FP64) from one point source; order 1
+    (first-order upwind) or 2 (the second-order stencil of Sec. II-B)."""
     lib = _lib.load()
     speed = np.ascontiguousarray(speed, dtype=np.float32)
     g = _lib.make_grid(speed.shape, dx, origin)
     src = np.ascontiguousarray(np.resize(np.asarray(src, dtype=np.float64), 3))
     T = np.empty(speed.shape, dtype=np.float64)
-    _lib.check(lib.pat_fmm_host(speed.ctypes.data, ctypes.byref(g), src.ctypes.data, T.ctypes.data),
-               "pat_fmm_host")
+    _lib.check(lib.pat_fmm_host(speed.ctypes.data, ctypes.byref(g), src.ctypes.data, int(order),
+                                T.ctypes.data), "pat_fmm_host")
     return T
 
 

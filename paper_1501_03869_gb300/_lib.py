@@ -34,6 +34,7 @@ EXPORTS = (
 )
 PAT_FLAG_HOST_MIRROR = 0x100
 PAT_FLAG_STAGED_SINGLE = 0x200
+PAT_FLAG_FMM_SECOND_ORDER = 0x400
 PAT_PLAN_AUTOTUNE = 0x1
 PAT_PLAN_GRAPH = 0x2
 
@@ -130,7 +131,7 @@ def load():
         lib.pat_bp_destroy.restype = _i
         lib.pat_bp_destroy.argtypes = [_vp]
         lib.pat_fmm_host.restype = _i
-        lib.pat_fmm_host.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _vp]
+        lib.pat_fmm_host.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp]
         lib.pat_table_host.restype = _i
         lib.pat_table_host.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp, _d, _i, _u,
                                        ctypes.POINTER(PatInfo), _vp, _vp, _vp]

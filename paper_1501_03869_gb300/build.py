@@ -50,7 +50,9 @@ def _compile(src, obj, extra):
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                "--expt-relaxed-constexpr", *extra, "-c", src, "-o", obj]
     else:
-        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall",
+        # no contraction into FMAs: the host fast marching gives the same bits on
+        # every host (its second-order update branches on exact ties)
+        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-ffp-contract=off",
                f"-I{os.path.join(os.path.dirname(nvcc), '..', 'include')}", "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

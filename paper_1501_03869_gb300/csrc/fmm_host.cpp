@@ -26,15 +26,15 @@ namespace patbp {
 
 namespace {
 constexpr uint8_t kFar = 0, kTrial = 1, kAccepted = 2, kGhost = 3;
+constexpr int kPad = 2;  // ghost layers per active side (the second-order stencil looks two nodes out)
 constexpr double kInf = std::numeric_limits<double>::infinity();
 }  // namespace
 
-FastMarcher::FastMarcher(const GridDesc& g, const std::vector<double>& slowness_h,
-                         const uint8_t* targets)
-    : g_(g) {
+FastMarcher::FastMarcher(const GridDesc& g, const float* speed, const uint8_t* targets, int order)
+    : g_(g), order_(order == 2 ? 2 : 1) {
   ptotal_ = 1;
   for (int d = 0; d < 3; ++d) {
-    pn_[d] = d < g.ndim ? g.n[d] + 2 : 1;
+    pn_[d] = d < g.ndim ? g.n[d] + 2 * kPad : 1;
     pstride_[d] = ptotal_;
     ptotal_ *= pn_[d];
   }
@@ -42,11 +42,13 @@ FastMarcher::FastMarcher(const GridDesc& g, const std::vector<double>& slowness_
   st_.assign(ptotal_, kGhost);
   pos_.assign(ptotal_, -1);
   hf_.assign(ptotal_, 0.0);
+  c_.assign(ptotal_, 0.0);
   wanted_.assign(ptotal_, 0);
   heap_.reserve(1 << 16);
   for (int64_t v = 0; v < g.total(); ++v) {
     int64_t pv = to_padded(v);
-    hf_[pv] = slowness_h[v];
+    c_[pv] = double(speed[v]);
+    hf_[pv] = g.dx / c_[pv];
     wanted_[pv] = targets ? (targets[v] ? 1 : 0) : 0;
   }
 }
@@ -56,7 +58,7 @@ int64_t FastMarcher::to_padded(int64_t v) const {
   for (int d = 0; d < 3; ++d) {
     int64_t c = v % g_.n[d];
     v /= g_.n[d];
-    p += (d < g_.ndim ? c + 1 : c) * pstride_[d];
+    p += (d < g_.ndim ? c + kPad : c) * pstride_[d];
   }
   return p;
 }
@@ -126,6 +128,56 @@ double FastMarcher::local_solve(int64_t pv, double hf) const {
   return root;
 }
 
+// Second-order local solve (the printed stencil of Sec. II-B, the one-sided
+// difference (3 T_i - 4 T_{i-1} + T_{i-2}) / 2h).  Per axis the upwind side is
+// the accepted neighbour with the smaller time (the lower side on a tie); when
+// the next node out on that side is accepted and not later, the axis enters as
+// (9/4)(T - (4 t1 - t2)/3)^2, else as the first-order (T - t1)^2.  Axes join in
+// increasing offset (a stable order) while the root lies above the next
+// offset; an axis whose inclusion leaves no real root is not included.
+// Unlike the first-order update the result can hinge on exact ties (the test
+// t2 <= t1 at a source in a cell centre), so the arithmetic is kept in one
+// fixed form -- one axis a + hf / sqrt(w), then sums W, M and C = sum w a^2 -
+// hf^2 grown axis by axis -- and this file is compiled without contraction
+// into FMAs, giving the same bits on every host.
+double FastMarcher::local_solve2(int64_t pv, double hf) const {
+  struct Axis {
+    double off, w;
+  } ax[3];
+  int m = 0;
+  for (int d = 0; d < g_.ndim; ++d) {
+    const int64_t s = pstride_[d];
+    const bool lo_ok = st_[pv - s] == kAccepted, hi_ok = st_[pv + s] == kAccepted;
+    if (!lo_ok && !hi_ok) continue;
+    const int64_t dir = (lo_ok && (!hi_ok || t_[pv - s] <= t_[pv + s])) ? -s : s;
+    const double t1 = t_[pv + dir];
+    const int64_t q2 = pv + 2 * dir;
+    if (st_[q2] == kAccepted && t_[q2] <= t1)
+      ax[m++] = Axis{(4.0 * t1 - t_[q2]) / 3.0, 2.25};
+    else
+      ax[m++] = Axis{t1, 1.0};
+  }
+  if (m == 0) return kInf;
+  // stable ascending order of at most three axes (swap only when strictly out of order)
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i + 1 < m; ++i)
+      if (ax[i].off > ax[i + 1].off) std::swap(ax[i], ax[i + 1]);
+  double W = ax[0].w, M = ax[0].w * ax[0].off, C = ax[0].w * ax[0].off * ax[0].off - hf * hf;
+  double root = ax[0].off + hf / std::sqrt(ax[0].w);
+  for (int k = 1; k < m; ++k) {
+    if (!(root > ax[k].off)) break;
+    const double W2 = W + ax[k].w, M2 = M + ax[k].w * ax[k].off;
+    const double C2 = C + ax[k].w * ax[k].off * ax[k].off;
+    const double disc = M2 * M2 - W2 * C2;
+    if (disc < 0.0) break;
+    W = W2;
+    M = M2;
+    C = C2;
+    root = (M + std::sqrt(disc)) / W;
+  }
+  return root;
+}
+
 bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_after,
                         int64_t n_targets) {
   // reset interior nodes; ghosts keep kGhost
@@ -133,10 +185,10 @@ bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_a
   std::fill(pos_.begin(), pos_.end(), -1);
   heap_.clear();
   const int nz = g_.ndim > 2 ? g_.n[2] : 1, ny = g_.ndim > 1 ? g_.n[1] : 1, nx = g_.n[0];
-  const int oz = g_.ndim > 2 ? 1 : 0, oy = g_.ndim > 1 ? 1 : 0;
+  const int oz = g_.ndim > 2 ? kPad : 0, oy = g_.ndim > 1 ? kPad : 0;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j) {
-      int64_t row = (k + oz) * pstride_[2] + (j + oy) * pstride_[1] + 1;
+      int64_t row = (k + oz) * pstride_[2] + (j + oy) * pstride_[1] + kPad;
       std::fill(st_.begin() + row, st_.begin() + row + nx, kFar);
     }
 
@@ -163,7 +215,7 @@ bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_a
     }
     int64_t pv = to_padded(v);
     if (st_[pv] == kAccepted) continue;
-    t_[pv] = std::sqrt(r2) * (hf_[pv] / g_.dx);
+    t_[pv] = std::sqrt(r2) / c_[pv];
     st_[pv] = kAccepted;
     seeds.push_back(pv);
     if (wanted_[pv]) --wanted_left;
@@ -175,7 +227,7 @@ bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_a
         int64_t q = pv + side * pstride_[d];
         uint8_t s = st_[q];
         if (s == kAccepted || s == kGhost) continue;
-        double cand = local_solve(q, hf_[q]);
+        double cand = order_ == 2 ? local_solve2(q, hf_[q]) : local_solve(q, hf_[q]);
         if (cand < t_[q]) {
           t_[q] = cand;
           if (s == kFar) {
@@ -214,7 +266,7 @@ bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_a
   int64_t v = 0;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j) {
-      int64_t row = (k + oz) * pstride_[2] + (j + oy) * pstride_[1] + 1;
+      int64_t row = (k + oz) * pstride_[2] + (j + oy) * pstride_[1] + kPad;
       for (int i = 0; i < nx; ++i, ++v) T[v] = st_[row + i] == kAccepted ? t_[row + i] : kInf;
     }
   return true;
@@ -315,16 +367,14 @@ bool layout_pixels(const GridDesc& g, const uint8_t* mask, int P, bool compact_o
 // ------------------------------------------------------------ table build --
 bool build_table(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
                  const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
-                 HostTable& out, std::string& err) {
+                 HostTable& out, std::string& err, int fmm_order) {
   auto t_start = std::chrono::steady_clock::now();
   const int64_t total = g.total();
-  std::vector<double> slowness_h(static_cast<size_t>(total));
   for (int64_t v = 0; v < total; ++v) {
     if (!(speed[v] > 0.0f) || !std::isfinite(speed[v])) {
       err = "speed must be finite and > 0 at every node";
       return false;
     }
-    slowness_h[v] = g.dx / double(speed[v]);
   }
   std::vector<int32_t> order;
   if (!layout_pixels(g, mask, P, compact_out, out, order, err)) return false;
@@ -346,7 +396,7 @@ bool build_table(const float* speed, const GridDesc& g, const double* sensors, i
   std::atomic<bool> failed{false};
   std::vector<int> span_max(n_threads, 0);
   auto worker = [&](unsigned tid) {
-    FastMarcher fm(g, slowness_h, wanted.data());
+    FastMarcher fm(g, speed, wanted.data(), fmm_order);
     std::vector<double> T;
     int span_local = 0;
     for (;;) {

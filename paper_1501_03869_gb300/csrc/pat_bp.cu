@@ -258,7 +258,7 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
   HostTable tab;
   std::string err;
   if (!build_table(speed_host, g, sensors_host, n_sensors, mask_host, dt, n_samples, h->P,
-                   h->compact, tab, err)) {
+                   h->compact, tab, err, (flags & PAT_FLAG_FMM_SECOND_ORDER) ? 2 : 1)) {
     free_handle(h);
     return fail(PAT_ERR_INVALID, err);
   }
@@ -751,17 +751,15 @@ extern "C" pat_status pat_bp_destroy(pat_bp_t h) {
 }
 
 extern "C" pat_status pat_fmm_host(const float* speed_host, const pat_grid* grid, const double* src_xyz,
-                                   double* T_out) {
+                                   int order, double* T_out) {
   if (!speed_host || !src_xyz || !T_out) return fail(PAT_ERR_INVALID, "NULL argument");
+  if (order != 1 && order != 2) return fail(PAT_ERR_INVALID, "order must be 1 or 2");
   GridDesc g;
   std::string err;
   if (!grid_from_abi(grid, g, err)) return fail(PAT_ERR_INVALID, err);
-  std::vector<double> slow(static_cast<size_t>(g.total()));
-  for (int64_t v = 0; v < g.total(); ++v) {
+  for (int64_t v = 0; v < g.total(); ++v)
     if (!(speed_host[v] > 0.0f)) return fail(PAT_ERR_INVALID, "speed must be > 0");
-    slow[v] = g.dx / double(speed_host[v]);
-  }
-  FastMarcher fm(g, slow, nullptr);
+  FastMarcher fm(g, speed_host, nullptr, order);
   std::vector<double> T;
   if (!fm.solve(src_xyz, T, std::numeric_limits<double>::infinity(), 0))
     return fail(PAT_ERR_INVALID, "source outside the grid");
@@ -784,7 +782,7 @@ extern "C" pat_status pat_table_host(const float* speed_host, const pat_grid* gr
   const int P = (flags & PAT_FLAG_TILE_256) ? 256 : 128;
   HostTable tab;
   if (!build_table(speed_host, g, sensors_host, n_sensors, mask_host, dt, n_samples, P, compact, tab,
-                   err))
+                   err, (flags & PAT_FLAG_FMM_SECOND_ORDER) ? 2 : 1))
     return fail(PAT_ERR_INVALID, err);
   std::memset(info, 0, sizeof(*info));
   info->n_pix = tab.n_pix;

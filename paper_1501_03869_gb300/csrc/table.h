@@ -54,21 +54,23 @@ struct HostTable {
   double build_seconds = 0.0;
 };
 
-// First-order Godunov fast marching from one point source (Sec. II-B) on the
-// host in FP64.  slowness_h[v] = dx / c(v); `targets` (optional, total()
-// bytes, nonzero = wanted) marks the nodes the caller needs.  solve() writes
+// Fast marching from one point source (Sec. II-B) on the host in FP64: the
+// first-order Godunov update, or (order 2) the printed second-order stencil.
+// speed[v] = c(v) > 0 at the nodes; `targets` (optional, total() bytes,
+// nonzero = wanted) marks the nodes the caller needs.  solve() writes
 // total() values to T; nodes never accepted hold +inf.  The march ends early
 // once the smallest tentative time exceeds `stop_after` (s) or once all
 // n_targets wanted nodes are accepted (n_targets = 0: never); values of
 // accepted nodes never depend on either early stop.
 class FastMarcher {
  public:
-  FastMarcher(const GridDesc& g, const std::vector<double>& slowness_h, const uint8_t* targets);
+  FastMarcher(const GridDesc& g, const float* speed, const uint8_t* targets, int order = 1);
   bool solve(const double* src, std::vector<double>& T, double stop_after, int64_t n_targets);
 
  private:
   GridDesc g_;
-  int pn_[3];            // padded extents (one ghost layer per active side)
+  int order_ = 1;
+  int pn_[3];            // padded extents (two ghost layers per active side)
   int64_t pstride_[3];
   int64_t ptotal_;
   std::vector<double> t_;     // padded arrival times
@@ -76,18 +78,20 @@ class FastMarcher {
   std::vector<int32_t> pos_;  // heap position of each padded node, -1 if absent
   std::vector<int64_t> heap_; // padded node ids
   std::vector<double> hf_;    // padded dx / c
+  std::vector<double> c_;     // padded c
   std::vector<uint8_t> wanted_;
   int64_t to_padded(int64_t v) const;
   void heap_up(int64_t i);
   void heap_down(int64_t i);
   bool key_less(int64_t a, int64_t b) const;
   double local_solve(int64_t pv, double hf) const;
+  double local_solve2(int64_t pv, double hf) const;
 };
 
 // Builds the table for every sensor with all host threads.
 bool build_table(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
                  const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
-                 HostTable& out, std::string& err);
+                 HostTable& out, std::string& err, int fmm_order = 1);
 
 // Pixel order used by the table: mask pixels (dense indices) sorted along the
 // space-filling curve of the grid.

@@ -307,3 +307,16 @@ def test_single_fp32_frame_host_round_trip_and_split_calls():
             assert np.array_equal(a, b) and np.array_equal(a, c)
         h = bp.reconstruct_host(sig)
         assert np.array_equal(h, bp.reconstruct(s).cpu().numpy())
+
+
+def test_second_order_table_fp32_parity():
+    """A handle built with the printed second-order stencil
+    (PAT_FLAG_FMM_SECOND_ORDER) against the oracle's order-2 table."""
+    w = synth.config1(n_frames=2)
+    pix = np.flatnonzero(w.mask.ravel())
+    T = travel_table("c1_order2", w.speed, w.dx, w.origin, w.sensors, pix, order=2)
+    ref = oracle.reconstruct(w.speed, w.dx, w.origin, w.sensors, w.signals, w.dt, w.mask, T=T)
+    got, _ = gpu_images(w, flags=_lib.PAT_FLAG_FMM_SECOND_ORDER)
+    assert_fp32_parity(got, ref, np.abs(w.p0).max())
+    first, _ = gpu_images(w)
+    assert not np.array_equal(first, got)

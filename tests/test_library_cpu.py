@@ -64,16 +64,55 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     assert e.value.status == _lib.PAT_ERR_INVALID
 
 
+@pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("shape,seed", [((40, 33), 1), ((12, 11, 10), 2)])
-def test_host_fmm_matches_oracle(shape, seed):
+def test_host_fmm_matches_oracle(shape, seed, order):
     rng = np.random.default_rng(seed)
     sp = rng.uniform(1400.0, 3000.0, shape).astype(np.float32)
     h = 1e-4
     origin = np.array([-3e-4, 2e-4, 1e-4])[: len(shape)]
     src = origin + np.array([s * h * 0.43 for s in shape[::-1]])
-    T_lib = fmm_host(sp, h, origin, src)
-    T_or = oracle.fmm_point(sp.astype(np.float64), h, origin, src)
+    T_lib = fmm_host(sp, h, origin, src, order=order)
+    T_or = oracle.fmm_point(sp.astype(np.float64), h, origin, src, order=order)
     assert np.allclose(T_lib, T_or, rtol=1e-12, atol=0)
+    if order == 2:
+        assert not np.allclose(T_lib, fmm_host(sp, h, origin, src, order=1), rtol=1e-6)
+
+
+def test_second_order_march_is_bitwise_the_oracles_at_exact_ties():
+    """A source at a cell centre makes tied neighbours, where the second-order
+    switch (second upwind node not later than the first) decides on the last
+    bit; the library's march evaluates the oracle's arithmetic, so the two
+    agree bit for bit there (and everywhere else)."""
+    for n, src_px in [(20, (13.5, 6.5)), (33, (16.0, 16.0))]:
+        h = 1e-4
+        sp = np.full((n, n), 1500.0, dtype=np.float32)
+        src = np.array(src_px) * h
+        T_lib = fmm_host(sp, h, np.zeros(2), src, order=2)
+        T_or = oracle.fmm_point(sp.astype(np.float64), h, np.zeros(2), src, order=2)
+        assert np.array_equal(T_lib, T_or)
+    w = synth.config1(n_frames=1)
+    for s in (0, 17):
+        T_lib = fmm_host(w.speed, w.dx, w.origin, w.sensors[s], order=2)
+        T_or = oracle.fmm_point(w.speed.astype(np.float64), w.dx, w.origin, w.sensors[s], order=2)
+        assert np.array_equal(T_lib, T_or)
+
+
+def test_second_order_table_matches_oracle():
+    """The table of a second-order handle (PAT_FLAG_FMM_SECOND_ORDER) holds the
+    oracle's order-2 arrival times."""
+    w = synth.config1(n_frames=1)
+    sensors = w.sensors[::8]
+    info, u, base, slot = table_host(w.speed, w.dx, w.origin, sensors, w.dt, w.nt, w.mask,
+                                     _lib.PAT_FLAG_FMM_SECOND_ORDER)
+    P = info["tile_pix"]
+    used = slot[slot >= 0]
+    T = oracle.travel_table(w.speed, w.dx, w.origin, sensors, used, order=2)
+    idx = np.flatnonzero(slot >= 0)
+    for s in range(sensors.shape[0]):
+        got = u[idx // P, s, idx % P].astype(np.float64) + base[idx // P, s]
+        inrec = T[s] / w.dt <= w.nt - 1
+        assert np.all(np.abs(got[inrec] - T[s][inrec] / w.dt) <= 1e-9 * T[s][inrec] / w.dt + 1e-4)
 
 
 def _check_table(w, flags=0, sensor_subset=None):
