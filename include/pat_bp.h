@@ -68,6 +68,12 @@ typedef void* pat_stream_t; /* a cudaStream_t; NULL = legacy default stream */
                                             (one-sided difference (3T_i - 4T_{i-1}
                                             + T_{i-2}) / 2h where the two upwind
                                             nodes are accepted and monotone)     */
+#define PAT_FLAG_GPU_TABLE 0x800u /* solve the arrival times of the table on the
+                                    current CUDA device (first-order scheme:
+                                    block-iterative fixed point of the same
+                                    Godunov update, equal bit for bit to the
+                                    host march, so the table is the same);
+                                    not with PAT_FLAG_FMM_SECOND_ORDER        */
 #define PAT_FLAG_STAGED_SINGLE 0x200u /* single frames through the staged (TMA
                                          pipeline) gather too; by default one
                                          frame takes the unstaged kernel, which
@@ -225,12 +231,22 @@ pat_status pat_bp_destroy(pat_bp_t h);
 pat_status pat_fmm_host(const float* speed_host, const pat_grid* grid, const double* src_xyz,
                         int order, double* T_out);
 
+/* pat_fmm_gpu -- first-order arrival times (Sec. II-B) of n_src point sources
+ * (src_xyz [n_src][3]) solved on the current CUDA device: the Godunov system
+ * iterated block by block to its fixed point with the host march's
+ * arithmetic.  T_out (host) [n_src][grid] receives FP64 times (s), equal to
+ * pat_fmm_host(order 1) of each source.  Synchronous; PAT_ERR_INVALID for a
+ * source outside the grid box, PAT_ERR_CUDA for a device failure. */
+pat_status pat_fmm_gpu(const float* speed_host, const pat_grid* grid, const double* src_xyz,
+                       int n_src, double* T_out);
+
 /* pat_table_host -- the table pat_bp_create would upload, built on the host
  * only (no GPU needed): same arguments as pat_bp_create.  info receives the
  * sizes; u_host [n_tiles][n_sensors][tile_pix], base_host [n_tiles][n_sensors]
  * and slot_host [n_tiles * tile_pix] are filled when non-NULL (call once with
  * NULL buffers to learn the sizes).  The split/sensor_warps fields of info
- * are not set.  CPU only. */
+ * are not set.  CPU only, except with PAT_FLAG_GPU_TABLE, which solves the
+ * arrival times on the current CUDA device (the result is the same). */
 pat_status pat_table_host(const float* speed_host, const pat_grid* grid, const double* sensors_host,
                           int n_sensors, const uint8_t* mask_host, double dt, int n_samples,
                           unsigned flags, pat_bp_info_t* info, float* u_host, int32_t* base_host,

@@ -20,7 +20,7 @@ import numpy as np
 from . import _lib
 from ._lib import PatError
 
-__all__ = ["BP", "Plan", "Server", "PatError", "fmm_host", "table_host", "reconstruct_multi",
+__all__ = ["BP", "Plan", "Server", "PatError", "fmm_host", "fmm_gpu", "table_host", "reconstruct_multi",
            "wait_timeout_probe", "DTYPES"]
 
 DTYPES = {"f32": _lib.PAT_F32, "bf16": _lib.PAT_BF16, "f16": _lib.PAT_F16}
@@ -433,6 +433,24 @@ def fmm_host(speed, dx, origin, src, order=1):
     _lib.check(lib.pat_fmm_host(speed.ctypes.data, ctypes.byref(g), src.ctypes.data, int(order),
                                 T.ctypes.data), "pat_fmm_host")
     return T
+
+
+def fmm_gpu(speed, dx, origin, sources):
+    """First-order arrival times of point sources ([n, 3] or one xyz) solved on
+    the current CUDA device; equal to fmm_host(order=1) of each source.
+    Returns [n, *speed.shape] FP64 (or speed.shape for one source)."""
+    lib = _lib.load()
+    speed = np.ascontiguousarray(speed, dtype=np.float32)
+    g = _lib.make_grid(speed.shape, dx, origin)
+    src = np.asarray(sources, dtype=np.float64)
+    one = src.ndim == 1
+    src = np.atleast_2d(src)
+    src = np.ascontiguousarray(np.concatenate(
+        [src, np.zeros((src.shape[0], 3 - src.shape[1]))], axis=1) if src.shape[1] < 3 else src)
+    T = np.empty((src.shape[0],) + speed.shape, dtype=np.float64)
+    _lib.check(lib.pat_fmm_gpu(speed.ctypes.data, ctypes.byref(g), src.ctypes.data, src.shape[0],
+                               T.ctypes.data), "pat_fmm_gpu")
+    return T[0] if one else T
 
 
 def table_host(speed, dx, origin, sensors, dt, n_samples, mask=None, flags=0):

@@ -178,6 +178,32 @@ double FastMarcher::local_solve2(int64_t pv, double hf) const {
   return root;
 }
 
+int source_corners(const GridDesc& g, const double* src, int64_t* node, double* dist) {
+  int cell[3] = {0, 0, 0};
+  for (int d = 0; d < g.ndim; ++d) {
+    if (g.n[d] < 2) return 0;
+    double x = (src[d] - g.origin[d]) / g.dx;
+    if (!(x >= 0.0) || !(x <= double(g.n[d] - 1))) return 0;
+    int i = int(std::floor(x));
+    cell[d] = std::min(i, g.n[d] - 2);
+  }
+  const int n = 1 << g.ndim;
+  for (int corner = 0; corner < n; ++corner) {
+    int64_t v = 0, mul = 1;
+    double r2 = 0.0;
+    for (int d = 0; d < g.ndim; ++d) {
+      int i = cell[d] + ((corner >> d) & 1);
+      double off = g.origin[d] + double(i) * g.dx - src[d];
+      r2 += off * off;
+      v += int64_t(i) * mul;
+      mul *= g.n[d];
+    }
+    node[corner] = v;
+    dist[corner] = std::sqrt(r2);
+  }
+  return n;
+}
+
 bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_after,
                         int64_t n_targets) {
   // reset interior nodes; ghosts keep kGhost
@@ -193,29 +219,16 @@ bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_a
     }
 
   // Source cell: corners accepted with distance times local slowness.
-  int cell[3] = {0, 0, 0};
-  for (int d = 0; d < g_.ndim; ++d) {
-    if (g_.n[d] < 2) return false;
-    double x = (src[d] - g_.origin[d]) / g_.dx;
-    if (!(x >= 0.0) || !(x <= double(g_.n[d] - 1))) return false;
-    int i = int(std::floor(x));
-    cell[d] = std::min(i, g_.n[d] - 2);
-  }
+  int64_t corner_node[8];
+  double corner_dist[8];
+  const int n_corners = source_corners(g_, src, corner_node, corner_dist);
+  if (n_corners == 0) return false;
   int64_t wanted_left = n_targets;
   std::vector<int64_t> seeds;
-  for (int corner = 0; corner < (1 << g_.ndim); ++corner) {
-    int64_t v = 0, mul = 1;
-    double r2 = 0.0;
-    for (int d = 0; d < g_.ndim; ++d) {
-      int i = cell[d] + ((corner >> d) & 1);
-      double off = g_.origin[d] + double(i) * g_.dx - src[d];
-      r2 += off * off;
-      v += int64_t(i) * mul;
-      mul *= g_.n[d];
-    }
-    int64_t pv = to_padded(v);
+  for (int corner = 0; corner < n_corners; ++corner) {
+    int64_t pv = to_padded(corner_node[corner]);
     if (st_[pv] == kAccepted) continue;
-    t_[pv] = std::sqrt(r2) / c_[pv];
+    t_[pv] = corner_dist[corner] / c_[pv];
     st_[pv] = kAccepted;
     seeds.push_back(pv);
     if (wanted_[pv]) --wanted_left;
@@ -365,9 +378,111 @@ bool layout_pixels(const GridDesc& g, const uint8_t* mask, int P, bool compact_o
 }
 
 // ------------------------------------------------------------ table build --
+namespace {
+
+// Windows and offsets of one sensor over all tiles from the arrival times of
+// the tile slots (time_at(t, p), s); returns the widest window.  Per tile the
+// window [base, base + len) holds floor(u), floor(u) + 1 of every pixel heard
+// within the record and one more sample for an offset that rounds up to the
+// next integer in FP32; base is a multiple of 8 and len of 8.
+template <class TimeAt>
+int fill_sensor(HostTable& out, int s, double dt, double last_u, TimeAt time_at) {
+  const int P = out.P, n_sensors = out.n_sensors;
+  int span = 0;
+  for (int t = 0; t < out.n_tiles; ++t) {
+    const int32_t* slot = out.slot_dense.data() + size_t(t) * P;
+    int64_t lo = std::numeric_limits<int64_t>::max(), hi = -1;
+    for (int p = 0; p < P; ++p) {
+      if (slot[p] < 0) continue;
+      double u = time_at(t, p) / dt;
+      if (!(u <= last_u)) continue;  // after the record (or unreached)
+      int64_t i = int64_t(std::floor(u));
+      lo = std::min(lo, i);
+      hi = std::max(hi, i);
+    }
+    float* urow = out.u.data() + (size_t(t) * n_sensors + s) * P;
+    if (hi < 0) {
+      out.base[size_t(t) * n_sensors + s] = 0;
+      continue;
+    }
+    int64_t base = lo & ~int64_t(7);
+    int len = (int(hi - base + 3) + 7) & ~7;
+    out.base[size_t(t) * n_sensors + s] = int32_t(base);
+    out.len[size_t(t) * n_sensors + s] = uint16_t(len);
+    span = std::max(span, len);
+    for (int p = 0; p < P; ++p) {
+      if (slot[p] < 0) continue;
+      double u = time_at(t, p) / dt;
+      if (!(u <= last_u)) continue;
+      urow[p] = float(u - double(base));
+    }
+  }
+  return span;
+}
+
+// Runs body(i) for i in [0, n) on all host threads; returns the largest result.
+template <class Body>
+int parallel_max(int n, Body body) {
+  unsigned n_threads = std::max(1u, std::thread::hardware_concurrency());
+  n_threads = std::min<unsigned>(n_threads, unsigned(std::max(n, 1)));
+  std::atomic<int> next{0};
+  std::vector<int> best(n_threads, 0);
+  auto worker = [&](unsigned tid) {
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      best[tid] = std::max(best[tid], body(i));
+    }
+  };
+  std::vector<std::thread> pool;
+  for (unsigned i = 0; i < n_threads; ++i) pool.emplace_back(worker, i);
+  for (auto& th : pool) th.join();
+  return *std::max_element(best.begin(), best.end());
+}
+
+// The GPU solver's batches; the host fills batch k while the GPU solves k + 1.
+bool table_times_gpu(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
+                     double dt, double last_u, double stop_after, HostTable& out, int& span,
+                     std::string& err) {
+  const int64_t n_slots = int64_t(out.n_tiles) * out.P;
+  const int batch = std::min(n_sensors, gpu_eikonal_batch(g, n_slots, size_t(8) << 30));
+  GpuEikonal* e = gpu_eikonal_create(g, speed, out.slot_dense, batch, err);
+  if (!e) return false;
+  std::vector<double> buf[2];
+  buf[0].resize(size_t(batch) * n_slots);
+  buf[1].resize(size_t(batch) * n_slots);
+  std::thread filler;
+  int fill_span = 0;
+  bool ok = true;
+  for (int s0 = 0, k = 0; s0 < n_sensors; s0 += batch, ++k) {
+    const int nb = std::min(batch, n_sensors - s0);
+    double* Tk = buf[k & 1].data();  // the filler still reads the other buffer
+    if (!gpu_eikonal_slot_times(e, sensors + 3 * size_t(s0), nb, stop_after, Tk, err)) {
+      ok = false;
+      break;
+    }
+    if (filler.joinable()) filler.join();
+    filler = std::thread([&out, &fill_span, Tk, s0, nb, n_slots, dt, last_u]() {
+      const int sp = parallel_max(nb, [&](int b) {
+        const double* Tb = Tk + size_t(b) * n_slots;
+        const int P = out.P;
+        return fill_sensor(out, s0 + b, dt, last_u,
+                           [Tb, P](int t, int p) { return Tb[size_t(t) * P + p]; });
+      });
+      fill_span = std::max(fill_span, sp);
+    });
+  }
+  if (filler.joinable()) filler.join();
+  gpu_eikonal_destroy(e);
+  span = std::max(span, fill_span);
+  return ok;
+}
+
+}  // namespace
+
 bool build_table(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
                  const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
-                 HostTable& out, std::string& err, int fmm_order) {
+                 HostTable& out, std::string& err, int fmm_order, bool gpu_eikonal) {
   auto t_start = std::chrono::steady_clock::now();
   const int64_t total = g.total();
   for (int64_t v = 0; v < total; ++v) {
@@ -375,6 +490,10 @@ bool build_table(const float* speed, const GridDesc& g, const double* sensors, i
       err = "speed must be finite and > 0 at every node";
       return false;
     }
+  }
+  if (gpu_eikonal && fmm_order != 1) {
+    err = "the GPU table build solves the first-order scheme only";
+    return false;
   }
   std::vector<int32_t> order;
   if (!layout_pixels(g, mask, P, compact_out, out, order, err)) return false;
@@ -384,70 +503,46 @@ bool build_table(const float* speed, const GridDesc& g, const double* sensors, i
   out.u.assign(size_t(n_tiles) * n_sensors * P, kOutOfRecord);
   out.base.assign(size_t(n_tiles) * n_sensors, 0);
   out.len.assign(size_t(n_tiles) * n_sensors, 0);
+  for (int s = 0; s < n_sensors; ++s) {
+    int64_t node[8];
+    double dist[8];
+    if (source_corners(g, sensors + 3 * s, node, dist) == 0) {
+      err = "a sensor lies outside the grid box";
+      return false;
+    }
+  }
 
-  std::vector<uint8_t> wanted(size_t(total), 0);
-  for (int32_t v : order) wanted[v] = 1;
   const double last_u = double(n_samples - 1);
   const double stop_after = last_u * dt * (1.0 + 1e-9);
-
-  unsigned n_threads = std::max(1u, std::thread::hardware_concurrency());
-  n_threads = std::min<unsigned>(n_threads, unsigned(n_sensors));
-  std::atomic<int> next{0};
-  std::atomic<bool> failed{false};
-  std::vector<int> span_max(n_threads, 0);
-  auto worker = [&](unsigned tid) {
-    FastMarcher fm(g, speed, wanted.data(), fmm_order);
-    std::vector<double> T;
-    int span_local = 0;
-    for (;;) {
-      int s = next.fetch_add(1);
-      if (s >= n_sensors || failed.load()) break;
-      if (!fm.solve(sensors + 3 * s, T, stop_after, n_pix)) {
-        failed.store(true);
-        break;
-      }
-      for (int t = 0; t < n_tiles; ++t) {
-        const int32_t* slot = out.slot_dense.data() + size_t(t) * P;
-        int64_t lo = std::numeric_limits<int64_t>::max(), hi = -1;
-        for (int p = 0; p < P; ++p) {
-          if (slot[p] < 0) continue;
-          double u = T[slot[p]] / dt;
-          if (!(u <= last_u)) continue;  // after the record (or unreached)
-          int64_t i = int64_t(std::floor(u));
-          lo = std::min(lo, i);
-          hi = std::max(hi, i);
-        }
-        float* urow = out.u.data() + (size_t(t) * n_sensors + s) * P;
-        if (hi < 0) {
-          out.base[size_t(t) * n_sensors + s] = 0;
-          continue;
-        }
-        int64_t base = lo & ~int64_t(7);
-        // window [base, base + len) holds floor(u), floor(u) + 1 and one more
-        // sample for an offset that rounds up to the next integer in FP32
-        int len = (int(hi - base + 3) + 7) & ~7;
-        out.base[size_t(t) * n_sensors + s] = int32_t(base);
-        out.len[size_t(t) * n_sensors + s] = uint16_t(len);
-        span_local = std::max(span_local, len);
-        for (int p = 0; p < P; ++p) {
-          if (slot[p] < 0) continue;
-          double u = T[slot[p]] / dt;
-          if (!(u <= last_u)) continue;
-          urow[p] = float(u - double(base));
-        }
-      }
-    }
-    span_max[tid] = span_local;
-  };
-  std::vector<std::thread> pool;
-  for (unsigned i = 0; i < n_threads; ++i) pool.emplace_back(worker, i);
-  for (auto& th : pool) th.join();
-  if (failed.load()) {
-    err = "a sensor lies outside the grid box";
-    return false;
-  }
   int span = 8;
-  for (int s : span_max) span = std::max(span, s);
+  if (gpu_eikonal) {
+    if (!table_times_gpu(speed, g, sensors, n_sensors, dt, last_u, stop_after, out, span, err))
+      return false;
+  } else {
+    std::vector<uint8_t> wanted(size_t(total), 0);
+    for (int32_t v : order) wanted[v] = 1;
+    unsigned n_threads = std::max(1u, std::thread::hardware_concurrency());
+    n_threads = std::min<unsigned>(n_threads, unsigned(n_sensors));
+    std::atomic<int> next{0};
+    std::vector<int> span_max(n_threads, 0);
+    auto worker = [&](unsigned tid) {
+      FastMarcher fm(g, speed, wanted.data(), fmm_order);
+      std::vector<double> T;
+      for (;;) {
+        int s = next.fetch_add(1);
+        if (s >= n_sensors) break;
+        fm.solve(sensors + 3 * s, T, stop_after, n_pix);  // sources checked above
+        const int32_t* slot = out.slot_dense.data();
+        span_max[tid] = std::max(span_max[tid], fill_sensor(out, s, dt, last_u, [&](int t, int p) {
+          return T[slot[size_t(t) * P + p]];
+        }));
+      }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned i = 0; i < n_threads; ++i) pool.emplace_back(worker, i);
+    for (auto& th : pool) th.join();
+    for (int sp : span_max) span = std::max(span, sp);
+  }
   out.W = span;
   out.build_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

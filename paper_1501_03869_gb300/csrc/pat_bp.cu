@@ -258,7 +258,8 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
   HostTable tab;
   std::string err;
   if (!build_table(speed_host, g, sensors_host, n_sensors, mask_host, dt, n_samples, h->P,
-                   h->compact, tab, err, (flags & PAT_FLAG_FMM_SECOND_ORDER) ? 2 : 1)) {
+                   h->compact, tab, err, (flags & PAT_FLAG_FMM_SECOND_ORDER) ? 2 : 1,
+                   (flags & PAT_FLAG_GPU_TABLE) != 0)) {
     free_handle(h);
     return fail(PAT_ERR_INVALID, err);
   }
@@ -767,6 +768,40 @@ extern "C" pat_status pat_fmm_host(const float* speed_host, const pat_grid* grid
   return PAT_OK;
 }
 
+extern "C" pat_status pat_fmm_gpu(const float* speed_host, const pat_grid* grid, const double* src_xyz,
+                                  int n_src, double* T_out) {
+  if (!speed_host || !src_xyz || !T_out) return fail(PAT_ERR_INVALID, "NULL argument");
+  if (n_src < 1) return fail(PAT_ERR_INVALID, "n_src must be >= 1");
+  GridDesc g;
+  std::string err;
+  if (!grid_from_abi(grid, g, err)) return fail(PAT_ERR_INVALID, err);
+  if (g.total() > INT32_MAX) return fail(PAT_ERR_INVALID, "grid too large");
+  for (int64_t v = 0; v < g.total(); ++v)
+    if (!(speed_host[v] > 0.0f) || !std::isfinite(speed_host[v]))
+      return fail(PAT_ERR_INVALID, "speed must be finite and > 0");
+  for (int s = 0; s < n_src; ++s) {
+    int64_t node[8];
+    double dist[8];
+    if (source_corners(g, src_xyz + 3 * size_t(s), node, dist) == 0)
+      return fail(PAT_ERR_INVALID, "source " + std::to_string(s) + " outside the grid");
+  }
+  std::vector<int32_t> all(size_t(g.total()));
+  for (int64_t v = 0; v < g.total(); ++v) all[v] = int32_t(v);
+  const int batch = std::min(n_src, gpu_eikonal_batch(g, g.total(), size_t(8) << 30));
+  GpuEikonal* e = gpu_eikonal_create(g, speed_host, all, batch, err);
+  if (!e) return fail(PAT_ERR_CUDA, err);
+  for (int s0 = 0; s0 < n_src; s0 += batch) {
+    const int nb = std::min(batch, n_src - s0);
+    if (!gpu_eikonal_slot_times(e, src_xyz + 3 * size_t(s0), nb, std::numeric_limits<double>::infinity(),
+                                T_out + size_t(s0) * g.total(), err)) {
+      gpu_eikonal_destroy(e);
+      return fail(PAT_ERR_CUDA, err);
+    }
+  }
+  gpu_eikonal_destroy(e);
+  return PAT_OK;
+}
+
 extern "C" pat_status pat_table_host(const float* speed_host, const pat_grid* grid,
                                      const double* sensors_host, int n_sensors,
                                      const uint8_t* mask_host, double dt, int n_samples,
@@ -782,7 +817,7 @@ extern "C" pat_status pat_table_host(const float* speed_host, const pat_grid* gr
   const int P = (flags & PAT_FLAG_TILE_256) ? 256 : 128;
   HostTable tab;
   if (!build_table(speed_host, g, sensors_host, n_sensors, mask_host, dt, n_samples, P, compact, tab,
-                   err, (flags & PAT_FLAG_FMM_SECOND_ORDER) ? 2 : 1))
+                   err, (flags & PAT_FLAG_FMM_SECOND_ORDER) ? 2 : 1, (flags & PAT_FLAG_GPU_TABLE) != 0))
     return fail(PAT_ERR_INVALID, err);
   std::memset(info, 0, sizeof(*info));
   info->n_pix = tab.n_pix;

@@ -88,10 +88,36 @@ class FastMarcher {
   double local_solve2(int64_t pv, double hf) const;
 };
 
-// Builds the table for every sensor with all host threads.
+// The grid cell holding a point source: its 2^ndim corners (dense indices)
+// and their distances to the source (m); the march fixes each corner at
+// distance / c.  Returns the number of corners, 0 if the source lies outside
+// the grid box or an active axis has fewer than two nodes.
+int source_corners(const GridDesc& g, const double* src, int64_t* node, double* dist);
+
+// Builds the table for every sensor.  The arrival times come from the host
+// march (all host threads) or, with gpu_eikonal (first order only), from the
+// GPU fixed-point solver below; either way the windows are filled on the host
+// by the same code, so both give the same table.
 bool build_table(const float* speed, const GridDesc& g, const double* sensors, int n_sensors,
                  const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
-                 HostTable& out, std::string& err, int fmm_order = 1);
+                 HostTable& out, std::string& err, int fmm_order = 1, bool gpu_eikonal = false);
+
+// First-order arrival times of batches of point sources on the current CUDA
+// device (eikonal.cu): the Godunov system iterated block by block to its
+// fixed point with the host march's arithmetic, so every value equals the
+// host march's.  create() uploads dx / c and the table's slot map (dense
+// index per tile slot, -1 padding) and sizes buffers for `batch` sources.
+// slot_times() solves nb <= batch sources (xyz per source) and writes
+// out[b][slot] = T (s), +inf for padding slots and for nodes later than
+// stop_after.  Errors return nullptr / false with a message in err.
+struct GpuEikonal;
+GpuEikonal* gpu_eikonal_create(const GridDesc& g, const float* speed,
+                               const std::vector<int32_t>& slot_dense, int batch, std::string& err);
+bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double stop_after,
+                            double* out, std::string& err);
+void gpu_eikonal_destroy(GpuEikonal* e);
+// sources per batch that fit a device-memory budget (bytes)
+int gpu_eikonal_batch(const GridDesc& g, int64_t n_slots, size_t budget);
 
 // Pixel order used by the table: mask pixels (dense indices) sorted along the
 // space-filling curve of the grid.
