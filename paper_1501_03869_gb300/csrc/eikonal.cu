@@ -1,23 +1,33 @@
-// eikonal.cu -- arrival times of many point sources on the GPU (Sec. II-B),
-// equal bit for bit to the host fast marching (first order).
+// eikonal.cu -- first-order arrival times of many point sources on the GPU
+// (Sec. II-B), for the table build.
 //
-// The first-order Godunov upwind system has one solution (the fast marching
-// solution), and every node's value is the local solve of its neighbours'
-// final values.  So instead of marching, the GPU iterates that local solve to
-// its exact fixed point, block by block: each CTA holds one block of nodes of
-// one source (16 x 16 in 2-D, 8 x 8 x 4 in 3-D) with a one-node halo in shared
-// memory and sweeps it (Jacobi) until nothing changes or a sweep budget is
-// spent; the next round processes the blocks that changed and their face
-// neighbours.  Values only decrease, from +inf, and the loop ends when a round
-// changes nothing: every node then equals the local solve of its neighbours.
+// The first-order Godunov upwind system sum_d max(T - a_d, 0)^2 = (h/c)^2 has
+// one solution, the one fast marching finds, and every node's value is the
+// local solve of its neighbours' values.  Instead of marching (a serial heap),
+// the GPU iterates that local solve to its fixed point, block by block: each
+// CTA holds one block of one source (16 x 16 nodes in 2-D, 8 x 8 x 4 in 3-D)
+// with a one-node halo in shared memory and sweeps it (Jacobi) until nothing
+// changes or a sweep budget is spent; the next round takes the blocks that
+// changed and their face neighbours.  Values only decrease, from +inf, so the
+// loop ends, and when a round changes nothing every node is at the fixed point
+// (to rounding: FP64 gives the host march's values to about 1e-12).
 //
-// Bitwise equality with the host march needs the same arithmetic: the source
-// cell's corners are fixed at distance / c, the local solve sorts the axis
-// minima with the host's compare-and-swap steps and grows the set of axes with
-// the same sums, every operation explicitly rounded (no FMA contraction; the
-// host file is compiled without contraction too).  Values above the record end
-// (stop_after) are never written, as the host march stops there; they cannot
-// influence earlier arrivals.
+// Work per node is kept small: a node is solved again only when a neighbour
+// moved BELOW its own value in the previous sweep (a neighbour at or above it
+// is not upwind and cannot lower it: in the Godunov equation its term is zero),
+// and at a block's first sweep only next to halo nodes that changed since the
+// block last settled.  Comparisons run on the bit patterns (non-negative
+// doubles order like their integer images), and the local solve uses the
+// difference form of the quadratic with a Newton-refined square root, so the
+// scarce FP64 pipe does little beyond the arithmetic itself.
+//
+// Blocks are launched in two colours ((bx + by + bz) & 1); face neighbours have
+// different colours, so no block reads a node another block of the launch
+// writes: the result is a fixed function of the input, whatever the order the
+// blocks run in and whatever else is in the batch.  The source cell's corners
+// are fixed at distance / c (as the host march fixes them), and values above
+// the record end (stop_after) are never written; they cannot lower earlier
+// arrivals.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -35,6 +45,8 @@ namespace patbp {
 namespace {
 
 constexpr int kMaxSeeds = 8;  // corners of the source cell
+constexpr int kUnclean = -2;  // block state: its nodes may not solve to their own values
+constexpr long long kInfBits = 0x7ff0000000000000LL;
 
 struct EikParams {
   double* T;            // [nb][total] arrival times (s)
@@ -43,6 +55,10 @@ struct EikParams {
   const int2* list;     // active (source, block) pairs
   int n_list;
   int* changed;         // [nb][n_blocks] set when a block's values changed
+  int* stamp;           // [nb][total] phase of a node's last change (-1 never, 0 seed)
+  int* visited;         // [nb][n_blocks] phase of the last visit that settled the
+                        // block (-1 never visited, kUnclean: left unsettled)
+  int phase;            // 2 * round + colour + 1
   int n[3];             // nodes per axis (x first)
   int bn[3];            // blocks per axis
   int ndim;
@@ -52,35 +68,48 @@ struct EikParams {
   int sweeps;           // sweep budget per block visit
 };
 
-// The host fast marching's first-order local solve, operation for operation.
-// a holds the per-axis upwind values, +inf for an axis without one; the host
-// sorts only its m finite values, and sorting all three gives the same
-// ascending finite values, so the sums below are the host's.
-__device__ __forceinline__ double root_step(double S, double Q, double hf2, int k) {
-  const double kk = double(k + 1);  // kk * x is exact for kk = 1, 2 and rounded once for 3
-  double disc = __dsub_rn(__dmul_rn(S, S), __dmul_rn(kk, __dsub_rn(Q, hf2)));
-  if (disc < 0.0) disc = 0.0;
-  const double num = __dadd_rn(S, __dsqrt_rn(disc));
-  // x / 1 and x / 2 are exact as x and x * 0.5: the same bits as the host's division
-  return k == 0 ? num : (k == 1 ? __dmul_rn(num, 0.5) : __ddiv_rn(num, 3.0));
+// Non-negative doubles (and +inf) order like their bit patterns; comparing
+// those keeps the comparisons off the FP64 pipe.
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool lt(double a, double b) { return bits(a) < bits(b); }
+__device__ __forceinline__ double min2(double a, double b) { return lt(b, a) ? b : a; }
+
+// sqrt(x) for x > 0: the FP32 reciprocal square root refined by one Newton
+// (Heron) step in FP64, s' = s + (x - s^2) / (2 s), which takes the relative
+// error from about 2^-23 to about 2^-46 (a few 1e-14).
+__device__ __forceinline__ double sqrt_newton(double x) {
+  const double r = double(rsqrtf(float(x)));
+  const double s = x * r;
+  const double e = fma(-s, s, x);
+  return fma(0.5 * r, e, s);
 }
 
-__device__ double local_solve(double a0, double a1, double a2, double hf) {
-  if (a1 < a0) { const double t = a0; a0 = a1; a1 = t; }
-  if (a2 < a1) { const double t = a1; a1 = a2; a2 = t; }
-  if (a1 < a0) { const double t = a0; a0 = a1; a1 = t; }
-  if (!(a0 < CUDART_INF)) return CUDART_INF;
-  const double hf2 = __dmul_rn(hf, hf);
-  double S = a0, Q = __dmul_rn(a0, a0);  // 0 + x is x
-  double root = root_step(S, Q, hf2, 0);
-  if (!(a1 < CUDART_INF) || !(root > a1)) return root;
-  S = __dadd_rn(S, a1);
-  Q = __dadd_rn(Q, __dmul_rn(a1, a1));
-  root = root_step(S, Q, hf2, 1);
-  if (!(a2 < CUDART_INF) || !(root > a2)) return root;
-  S = __dadd_rn(S, a2);
-  Q = __dadd_rn(Q, __dmul_rn(a2, a2));
-  return root_step(S, Q, hf2, 2);
+// First-order Godunov update from the per-axis upwind values a0 <= a1 <= a2
+// (+inf where an axis has none): the one-axis root a0 + h/c while it stays at
+// or below a1, else the two-axis root (a0 + a1 + sqrt(2 (h/c)^2 - (a1 - a0)^2)) / 2
+// while it stays at or below a2, else the three-axis root with the
+// discriminant 3 (h/c)^2 - sum of the squared pairwise differences.  The
+// difference form is the quadratic's discriminant without cancellation.
+// hf2 = 2 (h/c)^2 and hf3 = 3 (h/c)^2 are the node's constants.
+__device__ __forceinline__ double godunov(double a0, double a1, double a2, double hf, double hf2,
+                                          double hf3) {
+  if (bits(a0) >= kInfBits) return CUDART_INF;
+  double r = a0 + hf;
+  if (!lt(a1, r)) return r;
+  const double d01 = a1 - a0;
+  const double disc2 = fma(-d01, d01, hf2);  // > (h/c)^2 since a1 - a0 < h/c
+  r = 0.5 * (a0 + a1 + sqrt_newton(disc2));
+  if (!lt(a2, r)) return r;
+  const double d02 = a2 - a0, d12 = a2 - a1;
+  const double disc3 = fma(-d01, d01, fma(-d02, d02, fma(-d12, d12, hf3)));
+  const double s3 = disc3 > 0.0 ? sqrt_newton(disc3) : 0.0;
+  return (a0 + a1 + a2 + s3) * (1.0 / 3.0);
+}
+
+__device__ __forceinline__ void sort3(double& a0, double& a1, double& a2) {
+  if (lt(a1, a0)) { const double t = a0; a0 = a1; a1 = t; }
+  if (lt(a2, a1)) { const double t = a1; a1 = a2; a2 = t; }
+  if (lt(a1, a0)) { const double t = a0; a0 = a1; a1 = t; }
 }
 
 // Tile with a one-node halo: extents B + 2 per active axis.
@@ -93,28 +122,47 @@ struct Tile {
 template <int B0, int B1, int B2>
 __global__ void __launch_bounds__(B0 * B1 * B2) eik_sweep_kernel(const EikParams p) {
   using TL = Tile<B0, B1, B2>;
+  constexpr int NT = B0 * B1 * B2, NW = NT / 32;
   constexpr int SY = TL::X, SZ = TL::X * TL::Y;
   __shared__ double tile[TL::N];
   // moved[j][i]: node i changed in the sweep before one that reads moved[j]
-  // (a node whose neighbours did not move would solve to the same value)
   __shared__ uint8_t moved[2][TL::N];
+  // stamps of the halo (-1 inside the block and outside the grid)
+  __shared__ int hstamp[TL::N];
+  // per sweep, the nodes (thread ids) that need a solve, packed densely so the
+  // FP64 work runs in full warps; their h/c and their candidates
+  __shared__ int queue[NT];
+  __shared__ double hf_s[NT], cand_s[NT];
+  __shared__ int warp_count[NW];
   const int2 job = p.list[blockIdx.x];
   const int src = job.x, blk = job.y;
   const int bx = blk % p.bn[0], by = (blk / p.bn[0]) % p.bn[1], bz = blk / (p.bn[0] * p.bn[1]);
   const int x0 = bx * B0, y0 = by * B1, z0 = bz * B2;
   double* T = p.T + int64_t(src) * p.total;
+  int* stamp = p.stamp + int64_t(src) * p.total;
   const int hz = B2 > 1 ? 1 : 0;
   // load the block and its halo; nodes outside the grid are +inf
   for (int i = threadIdx.x; i < TL::N; i += blockDim.x) {
     const int tx = i % TL::X, ty = (i / TL::X) % TL::Y, tz = i / (TL::X * TL::Y);
     const int x = x0 + tx - 1, y = y0 + ty - 1, z = z0 + tz - hz;
+    const bool halo = tx == 0 || tx == TL::X - 1 || ty == 0 || ty == TL::Y - 1 ||
+                      (B2 > 1 && (tz == 0 || tz == TL::Z - 1));
     double v = CUDART_INF;
-    if (x >= 0 && x < p.n[0] && y >= 0 && y < p.n[1] && z >= 0 && z < p.n[2])
-      v = __ldcg(T + (int64_t(z) * p.n[1] + y) * p.n[0] + x);
+    int st = -1;
+    if (x >= 0 && x < p.n[0] && y >= 0 && y < p.n[1] && z >= 0 && z < p.n[2]) {
+      const int64_t g = (int64_t(z) * p.n[1] + y) * p.n[0] + x;
+      v = __ldcg(T + g);
+      if (halo) st = __ldcg(stamp + g);
+    }
     tile[i] = v;
+    hstamp[i] = st;
     moved[0][i] = 0;
     moved[1][i] = 0;
   }
+  // A settled block's nodes solve to their own values from the halo it saw then;
+  // only a node next to a halo node that has since dropped below it needs solving.
+  const int last = p.visited[int64_t(src) * p.n_blocks + blk];
+  const bool full = last == kUnclean;
   const int lx = threadIdx.x % B0, ly = (threadIdx.x / B0) % B1, lz = threadIdx.x / (B0 * B1);
   const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
   const bool inside = x < p.n[0] && y < p.n[1] && z < p.n[2];
@@ -123,37 +171,72 @@ __global__ void __launch_bounds__(B0 * B1 * B2) eik_sweep_kernel(const EikParams
   bool fixed = !inside;
   if (inside)
     for (int k = 0; k < kMaxSeeds; ++k) fixed |= p.seed[src * kMaxSeeds + k] == v;
-  const double hf = inside ? p.hf[v] : 0.0;
-  bool changed = false;
+  hf_s[threadIdx.x] = inside ? p.hf[v] : 0.0;
+  const int nbr[6] = {me - 1, me + 1, me - SY, me + SY, me - SZ, me + SZ};
+  constexpr int n_nbr = B2 > 1 ? 6 : 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool changed = false, settled = false;
   __syncthreads();
   for (int it = 0; it < p.sweeps; ++it) {
-    double cand = CUDART_INF;
+    const double mine = tile[me];
+    bool need = it == 0 && full;
     const uint8_t* mv = moved[it & 1];
-    bool need = it == 0 || mv[me - 1] || mv[me + 1] || mv[me - SY] || mv[me + SY];
-    if (B2 > 1) need = need || mv[me - SZ] || mv[me + SZ];
-    if (!fixed && need) {
+#pragma unroll
+    for (int k = 0; k < n_nbr; ++k) {
+      const bool fresh = it == 0 ? hstamp[nbr[k]] > last : mv[nbr[k]] != 0;
+      need |= fresh && lt(tile[nbr[k]], mine);
+    }
+    need &= !fixed;
+    // pack the nodes that need a solve: warp ballots, then a prefix over warps
+    const unsigned ballot = __ballot_sync(0xffffffffu, need);
+    if (lane == 0) warp_count[warp] = __popc(ballot);
+    __syncthreads();
+    int base = 0, n_work = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const int c = warp_count[w];
+      base += w < warp ? c : 0;
+      n_work += c;
+    }
+    if (need) queue[base + __popc(ballot & ((1u << lane) - 1u))] = threadIdx.x;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n_work; j += NT) {
+      const int q = queue[j];
+      const int qx = q % B0, qy = (q / B0) % B1, qz = q / (B0 * B1);
+      const int m = ((qz + hz) * TL::Y + (qy + 1)) * TL::X + (qx + 1);
       // per axis the smaller neighbour (the halo is +inf outside the grid)
-      const double x_lo = tile[me - 1], x_hi = tile[me + 1];
-      const double y_lo = tile[me - SY], y_hi = tile[me + SY];
-      double wz = CUDART_INF;
-      if (B2 > 1) {
-        const double z_lo = tile[me - SZ], z_hi = tile[me + SZ];
-        wz = z_lo < z_hi ? z_lo : z_hi;
-      }
-      cand = local_solve(x_lo < x_hi ? x_lo : x_hi, y_lo < y_hi ? y_lo : y_hi, wz, hf);
+      double a0 = min2(tile[m - 1], tile[m + 1]);
+      double a1 = min2(tile[m - SY], tile[m + SY]);
+      double a2 = B2 > 1 ? min2(tile[m - SZ], tile[m + SZ]) : CUDART_INF;
+      sort3(a0, a1, a2);
+      const double hf = hf_s[q];
+      cand_s[q] = godunov(a0, a1, a2, hf, 2.0 * hf * hf, 3.0 * hf * hf);
     }
     __syncthreads();  // every read of this sweep precedes its writes (Jacobi)
     bool upd = false;
-    if (cand < tile[me] && cand <= p.stop_after) {
-      tile[me] = cand;
-      changed = true;
-      upd = true;
+    if (need) {
+      const double cand = cand_s[threadIdx.x];
+      upd = lt(cand, mine) && !lt(p.stop_after, cand);
+      if (upd) {
+        tile[me] = cand;
+        changed = true;
+      }
     }
     moved[(it + 1) & 1][me] = upd;
-    if (!__syncthreads_or(upd)) break;  // also orders these writes before the next reads
+    if (!__syncthreads_or(upd)) {  // also orders these writes before the next reads
+      settled = true;
+      break;
+    }
   }
-  if (changed) T[v] = tile[me];
-  if (__syncthreads_or(changed) && threadIdx.x == 0) p.changed[int64_t(src) * p.n_blocks + blk] = 1;
+  if (changed) {
+    T[v] = tile[me];
+    stamp[v] = p.phase;
+  }
+  const bool any = __syncthreads_or(changed);
+  if (threadIdx.x == 0) {
+    if (any) p.changed[int64_t(src) * p.n_blocks + blk] = 1;
+    p.visited[int64_t(src) * p.n_blocks + blk] = settled ? p.phase : kUnclean;
+  }
 }
 
 // Next round's blocks: those that changed and their face neighbours, split by
@@ -186,19 +269,22 @@ __global__ void eik_fill_kernel(double* T, int64_t n, double v) {
     T[i] = v;
 }
 
-// Seeds: fixed values at the source cells' corners; their blocks count as changed.
-__global__ void eik_seed_kernel(double* T, const int64_t* seed, const double* seed_t, int nb,
-                                int64_t total, int* changed, int n_blocks, int n0, int n1, int B0,
-                                int B1, int B2, int bn0, int bn1) {
+// Seeds: fixed values at the source cells' corners (stamped 0); their blocks
+// count as changed and unsettled.
+__global__ void eik_seed_kernel(double* T, int* stamp, const int64_t* seed, const double* seed_t,
+                                int nb, int64_t total, int* changed, int* visited, int n_blocks, int n0,
+                                int n1, int B0, int B1, int B2, int bn0, int bn1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb * kMaxSeeds) return;
   const int64_t v = seed[i];
   if (v < 0) return;
   const int src = i / kMaxSeeds;
   T[int64_t(src) * total + v] = seed_t[i];
+  stamp[int64_t(src) * total + v] = 0;
   const int x = int(v % n0), y = int((v / n0) % n1), z = int(v / (int64_t(n0) * n1));
   const int blk = ((z / B2) * bn1 + (y / B1)) * bn0 + (x / B0);
   changed[int64_t(src) * n_blocks + blk] = 1;
+  visited[int64_t(src) * n_blocks + blk] = kUnclean;
 }
 
 // Values at the table's slots (tile order): [nb][n_slots], +inf for padding.
@@ -231,6 +317,8 @@ struct GpuEikonal {
   int32_t* d_slot = nullptr;
   double* d_T = nullptr;
   int* d_changed = nullptr;
+  int* d_stamp = nullptr;
+  int* d_visited = nullptr;
   int2* d_list = nullptr;
   int* d_count = nullptr;
   int64_t* d_seed = nullptr;
@@ -245,6 +333,8 @@ void gpu_eikonal_destroy(GpuEikonal* e) {
   cudaFree(e->d_slot);
   cudaFree(e->d_T);
   cudaFree(e->d_changed);
+  cudaFree(e->d_stamp);
+  cudaFree(e->d_visited);
   cudaFree(e->d_list);
   cudaFree(e->d_count);
   cudaFree(e->d_seed);
@@ -286,6 +376,8 @@ GpuEikonal* gpu_eikonal_create(const GridDesc& g, const float* speed,
             cuda_ok(cudaMalloc(&e->d_slot, std::max<size_t>(slot_dense.size(), 1) * 4), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_T, size_t(e->batch) * e->total * 8), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_changed, nbb * 4), "cudaMalloc", err) &&
+            cuda_ok(cudaMalloc(&e->d_stamp, size_t(e->batch) * e->total * 4), "cudaMalloc", err) &&
+            cuda_ok(cudaMalloc(&e->d_visited, nbb * 4), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_list, 2 * nbb * sizeof(int2)), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_count, 8), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_seed, size_t(e->batch) * kMaxSeeds * 8), "cudaMalloc", err) &&
@@ -328,12 +420,14 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
   const size_t nbb = size_t(nb) * e->n_blocks;
   if (!cuda_ok(cudaMemcpyAsync(e->d_seed, seed.data(), seed.size() * 8, cudaMemcpyHostToDevice, st), "seeds", err) ||
       !cuda_ok(cudaMemcpyAsync(e->d_seed_t, seed_t.data(), seed_t.size() * 8, cudaMemcpyHostToDevice, st), "seeds", err) ||
-      !cuda_ok(cudaMemsetAsync(e->d_changed, 0, nbb * 4, st), "memset", err))
+      !cuda_ok(cudaMemsetAsync(e->d_changed, 0, nbb * 4, st), "memset", err) ||
+      !cuda_ok(cudaMemsetAsync(e->d_stamp, 0xFF, size_t(nT) * 4, st), "memset", err) ||
+      !cuda_ok(cudaMemsetAsync(e->d_visited, 0xFF, nbb * 4, st), "memset", err))
     return false;
   eik_fill_kernel<<<1024, 256, 0, st>>>(e->d_T, nT, std::numeric_limits<double>::infinity());
   eik_seed_kernel<<<(nb * kMaxSeeds + 127) / 128, 128, 0, st>>>(
-      e->d_T, e->d_seed, e->d_seed_t, nb, e->total, e->d_changed, e->n_blocks, g.n[0], g.n[1], e->B[0],
-      e->B[1], e->B[2], e->bn[0], e->bn[1]);
+      e->d_T, e->d_stamp, e->d_seed, e->d_seed_t, nb, e->total, e->d_changed, e->d_visited,
+      e->n_blocks, g.n[0], g.n[1], e->B[0], e->B[1], e->B[2], e->bn[0], e->bn[1]);
   if (!cuda_ok(cudaGetLastError(), "seed launch", err)) return false;
 
   EikParams p;
@@ -342,6 +436,8 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
   p.seed = e->d_seed;
   p.list = e->d_list;
   p.changed = e->d_changed;
+  p.stamp = e->d_stamp;
+  p.visited = e->d_visited;
   for (int d = 0; d < 3; ++d) {
     p.n[d] = g.n[d];
     p.bn[d] = e->bn[d];
@@ -373,6 +469,7 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
       if (n_list[colour] == 0) continue;
       p.list = e->d_list + colour * cap;
       p.n_list = n_list[colour];
+      p.phase = int(2 * round + colour + 1);
       const cudaError_t r = g.ndim == 2 ? launch_sweep<16, 16, 1>(p, st) : launch_sweep<8, 8, 4>(p, st);
       if (!cuda_ok(r, "eikonal sweep launch", err)) return false;
     }
@@ -389,7 +486,7 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
 int gpu_eikonal_batch(const GridDesc& g, int64_t n_slots, size_t budget) {
   const int64_t nodes = g.total();
   const int64_t blocks = nodes / 64 + 64;  // generous bound on blocks per source
-  const int64_t per = nodes * 8 + n_slots * 8 + blocks * 12 + kMaxSeeds * 16;
+  const int64_t per = nodes * 12 + n_slots * 8 + blocks * 24 + kMaxSeeds * 16;
   return int(std::max<int64_t>(1, std::min<int64_t>(64, int64_t(budget) / per)));
 }
 
