@@ -59,6 +59,9 @@ struct EikParams {
   int* visited;         // [nb][n_blocks] phase of the last visit that settled the
                         // block (-1 never visited, kUnclean: left unsettled)
   int phase;            // 2 * round + colour + 1
+  int* pending;         // [nb][n_blocks] set while a block holds a lowering above tau
+  uint8_t* defer;       // [nb][total] set while a node's last solve was above tau
+  double tau;           // this round's acceptance bound (s)
   int n[3];             // nodes per axis (x first)
   int bn[3];            // blocks per axis
   int ndim;
@@ -120,7 +123,7 @@ struct Tile {
 };
 
 template <int B0, int B1, int B2>
-__global__ void __launch_bounds__(B0 * B1 * B2) eik_sweep_kernel(const EikParams p) {
+__global__ void __launch_bounds__(B0 * B1 * B2, 6) eik_sweep_kernel(const EikParams p) {
   using TL = Tile<B0, B1, B2>;
   constexpr int NT = B0 * B1 * B2, NW = NT / 32;
   constexpr int SY = TL::X, SZ = TL::X * TL::Y;
@@ -172,19 +175,21 @@ __global__ void __launch_bounds__(B0 * B1 * B2) eik_sweep_kernel(const EikParams
   if (inside)
     for (int k = 0; k < kMaxSeeds; ++k) fixed |= p.seed[src * kMaxSeeds + k] == v;
   hf_s[threadIdx.x] = inside ? p.hf[v] : 0.0;
-  const int nbr[6] = {me - 1, me + 1, me - SY, me + SY, me - SZ, me + SZ};
+  uint8_t* defer = p.defer + int64_t(src) * p.total;
+  const bool was_deferred = inside && __ldcg(defer + v) != 0;
   constexpr int n_nbr = B2 > 1 ? 6 : 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  bool changed = false, settled = false;
+  bool changed = false, settled = false, deferred = was_deferred;
   __syncthreads();
   for (int it = 0; it < p.sweeps; ++it) {
     const double mine = tile[me];
-    bool need = it == 0 && full;
+    bool need = it == 0 && (full || was_deferred);
     const uint8_t* mv = moved[it & 1];
 #pragma unroll
     for (int k = 0; k < n_nbr; ++k) {
-      const bool fresh = it == 0 ? hstamp[nbr[k]] > last : mv[nbr[k]] != 0;
-      need |= fresh && lt(tile[nbr[k]], mine);
+      const int off = (k & 1 ? 1 : -1) * (k < 2 ? 1 : (k < 4 ? SY : SZ));
+      const bool fresh = it == 0 ? hstamp[me + off] > last : mv[me + off] != 0;
+      need |= fresh && lt(tile[me + off], mine);
     }
     need &= !fixed;
     // pack the nodes that need a solve: warp ballots, then a prefix over warps
@@ -216,7 +221,12 @@ __global__ void __launch_bounds__(B0 * B1 * B2) eik_sweep_kernel(const EikParams
     bool upd = false;
     if (need) {
       const double cand = cand_s[threadIdx.x];
-      upd = lt(cand, mine) && !lt(p.stop_after, cand);
+      deferred = false;
+      if (lt(cand, mine) && !lt(p.stop_after, cand)) {
+        // a lowering above this round's bound waits for a later round
+        upd = !lt(p.tau, cand);
+        deferred = !upd;
+      }
       if (upd) {
         tile[me] = cand;
         changed = true;
@@ -232,10 +242,15 @@ __global__ void __launch_bounds__(B0 * B1 * B2) eik_sweep_kernel(const EikParams
     T[v] = tile[me];
     stamp[v] = p.phase;
   }
+  if (deferred != was_deferred) defer[v] = deferred;
   const bool any = __syncthreads_or(changed);
+  const bool waits = __syncthreads_or(deferred);
   if (threadIdx.x == 0) {
-    if (any) p.changed[int64_t(src) * p.n_blocks + blk] = 1;
-    p.visited[int64_t(src) * p.n_blocks + blk] = settled ? p.phase : kUnclean;
+    const int64_t b = int64_t(src) * p.n_blocks + blk;
+    if (any) p.changed[b] = 1;
+    p.pending[b] = waits;
+    // deferred nodes are remembered one by one, so they do not unsettle the block
+    p.visited[b] = settled ? p.phase : kUnclean;
   }
 }
 
@@ -244,14 +259,14 @@ __global__ void __launch_bounds__(B0 * B1 * B2) eik_sweep_kernel(const EikParams
 // have different colours, so the blocks of one colour never read a node that
 // another block of the launch writes: each launch, and so the whole solve, is
 // a fixed function of its input whatever order the blocks run in.
-__global__ void eik_next_kernel(const int* changed, int nb, int n_blocks, int bn0, int bn1, int bn2,
-                                int2* list, int64_t cap, int* n_list) {
+__global__ void eik_next_kernel(const int* changed, const int* pending, int nb, int n_blocks, int bn0,
+                                int bn1, int bn2, int2* list, int64_t cap, int* n_list) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= int64_t(nb) * n_blocks) return;
   const int src = int(i / n_blocks), blk = int(i - int64_t(src) * n_blocks);
   const int bx = blk % bn0, by = (blk / bn0) % bn1, bz = blk / (bn0 * bn1);
   const int* c = changed + int64_t(src) * n_blocks;
-  bool act = c[blk] != 0;
+  bool act = c[blk] != 0 || pending[int64_t(src) * n_blocks + blk] != 0;
   act |= bx > 0 && c[blk - 1];
   act |= bx + 1 < bn0 && c[blk + 1];
   act |= by > 0 && c[blk - bn0];
@@ -319,6 +334,9 @@ struct GpuEikonal {
   int* d_changed = nullptr;
   int* d_stamp = nullptr;
   int* d_visited = nullptr;
+  int* d_pending = nullptr;
+  uint8_t* d_defer = nullptr;
+  double hf_mean = 0.0, hf_max = 0.0;
   int2* d_list = nullptr;
   int* d_count = nullptr;
   int64_t* d_seed = nullptr;
@@ -335,6 +353,8 @@ void gpu_eikonal_destroy(GpuEikonal* e) {
   cudaFree(e->d_changed);
   cudaFree(e->d_stamp);
   cudaFree(e->d_visited);
+  cudaFree(e->d_pending);
+  cudaFree(e->d_defer);
   cudaFree(e->d_list);
   cudaFree(e->d_count);
   cudaFree(e->d_seed);
@@ -369,7 +389,10 @@ GpuEikonal* gpu_eikonal_create(const GridDesc& g, const float* speed,
   for (int64_t v = 0; v < e->total; ++v) {
     e->c[v] = double(speed[v]);
     hf[v] = g.dx / e->c[v];
+    e->hf_mean += hf[v];
+    e->hf_max = std::max(e->hf_max, hf[v]);
   }
+  e->hf_mean /= double(e->total);
   const size_t nbb = size_t(e->batch) * e->n_blocks;
   bool ok = cuda_ok(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking), "stream", err) &&
             cuda_ok(cudaMalloc(&e->d_hf, size_t(e->total) * 8), "cudaMalloc", err) &&
@@ -378,6 +401,8 @@ GpuEikonal* gpu_eikonal_create(const GridDesc& g, const float* speed,
             cuda_ok(cudaMalloc(&e->d_changed, nbb * 4), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_stamp, size_t(e->batch) * e->total * 4), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_visited, nbb * 4), "cudaMalloc", err) &&
+            cuda_ok(cudaMalloc(&e->d_pending, nbb * 4), "cudaMalloc", err) &&
+            cuda_ok(cudaMalloc(&e->d_defer, size_t(e->batch) * e->total), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_list, 2 * nbb * sizeof(int2)), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_count, 8), "cudaMalloc", err) &&
             cuda_ok(cudaMalloc(&e->d_seed, size_t(e->batch) * kMaxSeeds * 8), "cudaMalloc", err) &&
@@ -422,7 +447,9 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
       !cuda_ok(cudaMemcpyAsync(e->d_seed_t, seed_t.data(), seed_t.size() * 8, cudaMemcpyHostToDevice, st), "seeds", err) ||
       !cuda_ok(cudaMemsetAsync(e->d_changed, 0, nbb * 4, st), "memset", err) ||
       !cuda_ok(cudaMemsetAsync(e->d_stamp, 0xFF, size_t(nT) * 4, st), "memset", err) ||
-      !cuda_ok(cudaMemsetAsync(e->d_visited, 0xFF, nbb * 4, st), "memset", err))
+      !cuda_ok(cudaMemsetAsync(e->d_visited, 0xFF, nbb * 4, st), "memset", err) ||
+      !cuda_ok(cudaMemsetAsync(e->d_pending, 0, nbb * 4, st), "memset", err) ||
+      !cuda_ok(cudaMemsetAsync(e->d_defer, 0, size_t(nT), st), "memset", err))
     return false;
   eik_fill_kernel<<<1024, 256, 0, st>>>(e->d_T, nT, std::numeric_limits<double>::infinity());
   eik_seed_kernel<<<(nb * kMaxSeeds + 127) / 128, 128, 0, st>>>(
@@ -438,6 +465,16 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
   p.changed = e->d_changed;
   p.stamp = e->d_stamp;
   p.visited = e->d_visited;
+  p.pending = e->d_pending;
+  p.defer = e->d_defer;
+  // Rounds accept lowerings up to tau = (round + 1) * dtau (a bucketed
+  // Dijkstra order): a node takes a value only once the values upwind of it
+  // are final or nearly so, instead of passing provisional values far ahead
+  // of the front.  dtau is a quarter block edge of the mean medium (8 x 8 x 4
+  // blocks: two node spacings; 16 x 16: four), or 1/1024 of the time span
+  // when that is coarser.
+  const double t_end = std::min(stop_after, double(g.n[0] + g.n[1] + g.n[2]) * e->hf_max);
+  const double dtau = std::max(0.25 * e->B[0] * e->hf_mean, t_end / 1024.0);
   for (int d = 0; d < 3; ++d) {
     p.n[d] = g.n[d];
     p.bn[d] = e->bn[d];
@@ -459,7 +496,8 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
     if (!cuda_ok(cudaMemsetAsync(e->d_count, 0, 8, st), "memset", err)) return false;
     const int64_t nthr = int64_t(nb) * e->n_blocks;
     eik_next_kernel<<<unsigned((nthr + 255) / 256), 256, 0, st>>>(
-        e->d_changed, nb, e->n_blocks, e->bn[0], e->bn[1], e->bn[2], e->d_list, cap, e->d_count);
+        e->d_changed, e->d_pending, nb, e->n_blocks, e->bn[0], e->bn[1], e->bn[2], e->d_list, cap,
+        e->d_count);
     if (!cuda_ok(cudaMemcpyAsync(n_list, e->d_count, 8, cudaMemcpyDeviceToHost, st), "count", err) ||
         !cuda_ok(cudaStreamSynchronize(st), "eikonal round", err))
       return false;
@@ -470,6 +508,7 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
       p.list = e->d_list + colour * cap;
       p.n_list = n_list[colour];
       p.phase = int(2 * round + colour + 1);
+      p.tau = double(round + 1) * dtau;
       const cudaError_t r = g.ndim == 2 ? launch_sweep<16, 16, 1>(p, st) : launch_sweep<8, 8, 4>(p, st);
       if (!cuda_ok(r, "eikonal sweep launch", err)) return false;
     }
@@ -486,7 +525,7 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
 int gpu_eikonal_batch(const GridDesc& g, int64_t n_slots, size_t budget) {
   const int64_t nodes = g.total();
   const int64_t blocks = nodes / 64 + 64;  // generous bound on blocks per source
-  const int64_t per = nodes * 12 + n_slots * 8 + blocks * 24 + kMaxSeeds * 16;
+  const int64_t per = nodes * 13 + n_slots * 8 + blocks * 28 + kMaxSeeds * 16;
   return int(std::max<int64_t>(1, std::min<int64_t>(64, int64_t(budget) / per)));
 }
 
