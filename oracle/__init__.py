@@ -17,9 +17,14 @@ only compiles it with gcc on first use and marshals numpy arrays:
 * :func:`constant_table` -- the conventional back projection's time of flight
   for a constant sound speed (Sec. II-C; Sec. III compares at 1560 m/s):
   straight-line distance over c0.
+* :func:`solid_angle_weights` -- the weight of the exact back projection that
+  Eq. (BP) approximates (Sec. II-C): the share of the total solid angle (2-D:
+  plane angle) that a sensor's element subtends at a pixel, written out in
+  numpy from its definition.
 * :func:`preprocess` -- Sec. II-C, Eq. (BP) integrand b = 2p - 2t dp/dt.
 * :func:`sample` / :func:`bp` -- Sec. II-C, Eq. (BP), P_j = sum_s w_s b_s(T_sj/dt)
-  with linear interpolation, zero after the last sample.
+  with linear interpolation, zero after the last sample; the weights may be
+  per sensor or per (sensor, pixel) pair.
 * :func:`reconstruct` -- the whole chain on a grid with a mask, dense output.
 """
 from __future__ import annotations
@@ -70,6 +75,8 @@ def _load():
             lib.oracle_sample.restype = ctypes.c_double
             lib.oracle_bp.argtypes = [ctypes.c_int64, ctypes.c_int64, _dp, ctypes.c_double,
                                       ctypes.c_int64, _dp, _dp, _dp]
+            lib.oracle_bp_pairs.argtypes = [ctypes.c_int64, ctypes.c_int64, _dp, ctypes.c_double,
+                                            ctypes.c_int64, _dp, _dp, _dp]
             _lib = lib
     return _lib
 
@@ -163,6 +170,27 @@ def constant_table(shape, h, origin, sensors, pix, c0):
     return out
 
 
+def solid_angle_weights(shape, h, origin, sensors, normals, elem, omega0, pix):
+    """W[s, j] = elem_s (n_s . (x_j - r_s)) / |x_j - r_s|^d / omega0: the share
+    of the solid angle omega0 (2-D: plane angle) that sensor s's element
+    subtends at node pix[j] -- the weight of the exact back projection that
+    Eq. (BP) approximates (Sec. II-C).  d = len(shape); n_s is the element's
+    normal towards the imaged region (normalised here), elem_s its length
+    (2-D) or area (3-D).  In 2-D only x and y of sensors and normals count."""
+    sensors = np.asarray(sensors, dtype=np.float64)
+    normals = np.asarray(normals, dtype=np.float64)
+    elem = np.asarray(elem, dtype=np.float64)
+    nd = len(shape)
+    pos = node_positions(shape, h, origin, pix)[:, :nd]
+    out = np.empty((sensors.shape[0], len(pix)), dtype=np.float64)
+    for s in range(sensors.shape[0]):
+        n = normals[s, :nd] / np.sqrt(np.sum(normals[s, :nd] ** 2))
+        v = pos - sensors[s, :nd]
+        r = np.sqrt(np.sum(v * v, axis=1))
+        out[s] = elem[s] * (v @ n) / r ** nd / float(omega0)
+    return out
+
+
 def preprocess(p, dt):
     """b = 2p - 2t dp/dt along the last axis (Eq. (BP) integrand)."""
     lib = _load()
@@ -183,7 +211,9 @@ def sample(b, u):
 
 
 def bp(T, p, dt, weights=None):
-    """P_j = sum_s w_s b_s(T[s, j] / dt); T [ns, npix], p [ns, nt]."""
+    """P_j = sum_s w_s b_s(T[s, j] / dt); T [ns, npix], p [ns, nt].  weights
+    is None (1/ns), [ns] per sensor, or [ns, npix] per (sensor, pixel) pair
+    (the exact back projection's solid-angle weights)."""
     lib = _load()
     T = np.ascontiguousarray(T, dtype=np.float64)
     p = np.ascontiguousarray(p, dtype=np.float64)
@@ -191,8 +221,12 @@ def bp(T, p, dt, weights=None):
     assert p.shape[0] == ns
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     out = np.empty(npix, dtype=np.float64)
-    rc = lib.oracle_bp(ns, npix, _d(T), float(dt), p.shape[1], _d(p),
-                       _d(w) if w is not None else None, _d(out))
+    if w is not None and w.ndim == 2:
+        assert w.shape == T.shape
+        rc = lib.oracle_bp_pairs(ns, npix, _d(T), float(dt), p.shape[1], _d(p), _d(w), _d(out))
+    else:
+        rc = lib.oracle_bp(ns, npix, _d(T), float(dt), p.shape[1], _d(p),
+                           _d(w) if w is not None else None, _d(out))
     _check(rc, "bp")
     return out
 

@@ -32,7 +32,11 @@
  *   - weights w_i default to 1/N_s and the integrand carries the factor 2 of
  *     the universal back projection (the paper's Eq. (BP) is that sum times
  *     N_s/2, a pure scale);
- *   - linear interpolation of b (not of p and dp/dt separately).
+ *   - linear interpolation of b (not of p and dp/dt separately);
+ *   - the exact back projection that Eq. (BP) approximates (Sec. II-C) weighs
+ *     each sensor by the solid angle its element subtends at the pixel; the
+ *     sum with a weight per (sensor, pixel) pair is oracle_bp_pairs, the
+ *     weights themselves are formed in the Python half of the oracle.
  *
  * Everything is double precision; no blocking, fusion or reordering beyond the
  * steps above.
@@ -433,6 +437,28 @@ int oracle_bp(int64_t ns, int64_t npix, const double* T, double dt, int64_t nt,
       double ws = w ? w[s] : 1.0 / (double)ns;
       acc += ws * oracle_sample(b + s * nt, nt, T[s * npix + j] / dt);
     }
+    out[j] = acc;
+  }
+  free(b);
+  return ORACLE_OK;
+}
+
+/* P_j = sum_s W[s][j] b_s(T[s][j] / dt): Eq. (BP) with one weight per
+ * (sensor, pixel) pair, the sensors summed in order.  With W[s][j] = w_s for
+ * every j it is oracle_bp.
+ *
+ * T[ns][npix], W[ns][npix], p[ns][nt], out[npix] as in oracle_bp.
+ */
+int oracle_bp_pairs(int64_t ns, int64_t npix, const double* T, double dt, int64_t nt,
+                    const double* p, const double* W, double* out) {
+  if (ns < 1 || npix < 0 || !T || !p || !W || !out || nt < 2 || !(dt > 0)) return ORACLE_ERR_ARG;
+  double* b = (double*)malloc((size_t)(ns * nt) * sizeof(double));
+  if (!b) return ORACLE_ERR_NOMEM;
+  for (int64_t s = 0; s < ns; ++s) oracle_preprocess(p + s * nt, nt, dt, b + s * nt);
+  for (int64_t j = 0; j < npix; ++j) {
+    double acc = 0.0;
+    for (int64_t s = 0; s < ns; ++s)
+      acc += W[s * npix + j] * oracle_sample(b + s * nt, nt, T[s * npix + j] / dt);
     out[j] = acc;
   }
   free(b);

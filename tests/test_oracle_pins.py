@@ -617,3 +617,100 @@ def test_second_order_accept_order_and_causality():
     popped = T.ravel()[order]
     assert np.all(np.diff(popped) >= -1e-15 * popped.max())
     assert np.isfinite(T).all()
+
+
+# ------------------------------------------------ exact back-projection weights --
+# Sec. II-C: Eq. (BP) approximates the exact back projection, which weighs each
+# sensor by the solid angle its element subtends at the pixel.  The weights are
+# pinned by Gauss's theorem for angles: a closed curve (surface) is seen under
+# the full angle 2 pi (4 pi) from every point inside it and under 0 from every
+# point outside, so the weights of a closed array sum to 1 inside and 0 outside.
+def _ring_geometry(n, radius, centre=(0.0, 0.0)):
+    th = 2.0 * np.pi * (np.arange(n) + 0.25) / n
+    sens = np.stack([centre[0] + radius * np.cos(th), centre[1] + radius * np.sin(th),
+                     np.zeros(n)], axis=1)
+    normals = -np.stack([np.cos(th), np.sin(th), np.zeros(n)], axis=1)
+    return sens, normals, np.full(n, 2.0 * np.pi * radius / n)
+
+
+def test_solid_angle_ring_sums_to_one_inside_and_zero_outside():
+    shape, h = (41, 41), 1e-3
+    origin = np.array([-20e-3, -20e-3, 0.0])
+    R = 12.3e-3
+    sens, nrm, elem = _ring_geometry(256, R)
+    pix = np.arange(41 * 41)
+    W = oracle.solid_angle_weights(shape, h, origin, sens, nrm, elem, 2.0 * np.pi, pix)
+    r = np.linalg.norm(oracle.node_positions(shape, h, origin, pix)[:, :2], axis=1)
+    tot = W.sum(axis=0)
+    inside, outside = r < 0.7 * R, r > 1.3 * R
+    assert inside.sum() > 100 and outside.sum() > 100
+    assert np.abs(tot[inside] - 1.0).max() < 1e-12
+    assert np.abs(tot[outside]).max() < 1e-12
+    # the centre sees every element of the ring at the same angle: 1/N each
+    c = np.argmin(r)
+    assert r[c] == 0.0 and np.allclose(W[:, c], 1.0 / 256, rtol=1e-13, atol=0)
+
+
+def test_solid_angle_ellipse_with_unequal_elements():
+    """A non-circular array: an ellipse sampled at equal parameter steps, so the
+    elements differ in length and the normals are not radial."""
+    shape, h = (41, 41), 1e-3
+    origin = np.array([-20e-3, -20e-3, 0.0])
+    a, b, n = 15e-3, 9e-3, 512
+    th = 2.0 * np.pi * np.arange(n) / n
+    sens = np.stack([a * np.cos(th), b * np.sin(th), np.zeros(n)], axis=1)
+    out_n = np.stack([b * np.cos(th), a * np.sin(th), np.zeros(n)], axis=1)
+    speed = np.hypot(a * np.sin(th), b * np.cos(th))  # |dr/dtheta|
+    elem = speed * 2.0 * np.pi / n
+    pix = np.arange(41 * 41)
+    W = oracle.solid_angle_weights(shape, h, origin, sens, -out_n, elem, 2.0 * np.pi, pix)
+    pos = oracle.node_positions(shape, h, origin, pix)
+    q = (pos[:, 0] / a) ** 2 + (pos[:, 1] / b) ** 2
+    tot = W.sum(axis=0)
+    assert np.abs(tot[q < 0.5] - 1.0).max() < 1e-10
+    assert np.abs(tot[q > 2.0]).max() < 1e-10
+    # outward normals see the full angle with the opposite sign
+    Wout = oracle.solid_angle_weights(shape, h, origin, sens, out_n, elem, 2.0 * np.pi, pix)
+    assert np.allclose(Wout, -W, rtol=0, atol=1e-15)
+
+
+def _fibonacci_sphere(n, radius):
+    k = np.arange(n) + 0.5
+    z = 1.0 - 2.0 * k / n
+    phi = np.pi * (1.0 + 5.0 ** 0.5) * k
+    rho = np.sqrt(1.0 - z * z)
+    return radius * np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+
+
+def test_solid_angle_sphere_centre_exact_interior_converges():
+    """3-D: equal-area elements of a sphere (Fibonacci lattice) with inward
+    normals.  At the centre every weight is exactly 1/N; inside, the weights sum
+    to 1 up to the lattice's quadrature error, which falls as N grows."""
+    shape, h = (21, 21, 21), 1e-3
+    origin = np.array([-10e-3] * 3)
+    R = 30e-3
+    pix = np.arange(21 ** 3)
+    r = np.linalg.norm(oracle.node_positions(shape, h, origin, pix), axis=1)
+    inner = r <= 0.5 * R
+    errs = []
+    for n in (500, 2000):
+        S = _fibonacci_sphere(n, R)
+        W = oracle.solid_angle_weights(shape, h, origin, S, -S / R, np.full(n, 4 * np.pi * R * R / n),
+                                       4.0 * np.pi, pix)
+        c = np.argmin(r)
+        assert r[c] == 0.0 and np.allclose(W[:, c], 1.0 / n, rtol=1e-13, atol=0)
+        errs.append(np.abs(W.sum(axis=0)[inner] - 1.0).max())
+    assert errs[1] < 3e-5 and errs[1] < errs[0] / 3
+
+
+def test_bp_with_pair_weights_reduces_to_sensor_weights():
+    """Weights per (sensor, pixel) that do not depend on the pixel give the
+    per-sensor sum bit for bit."""
+    rng = np.random.default_rng(7)
+    ns, npix, nt, dt = 9, 40, 64, 1e-8
+    T = rng.uniform(-2, nt + 2, (ns, npix)) * dt
+    p = rng.standard_normal((ns, nt))
+    w = rng.uniform(0.1, 1.0, ns)
+    a = oracle.bp(T, p, dt, w)
+    b = oracle.bp(T, p, dt, np.repeat(w[:, None], npix, axis=1))
+    assert np.array_equal(a, b)
