@@ -140,6 +140,30 @@ pat_status pat_bp_create_constant(double c0, const pat_grid* grid, const double*
                                   const float* weights_host, double dt, int n_samples,
                                   unsigned flags, pat_bp_t* out);
 
+/* pat_bp_set_solid_angle -- switch a handle to the exact back projection that
+ * Eq. (BP) approximates (Sec. II-C notes the approximation assumes a circular
+ * scan with a radius much larger than the imaged region): every term is
+ * weighted by the share of the full angle that the sensor's element subtends
+ * at the pixel,
+ *     w_s(r) = elem_s (n_s . (r - r_s)) / |r - r_s|^d / omega0,
+ * d = 2 for a 2-D grid (plane angle; x and y only) and 3 for a 3-D grid.  This
+ * replaces the per-sensor weights of the handle.  The kernel evaluates w from
+ * 32 bytes per (pixel tile, sensor) and 16 per pixel (FP32, relative error a
+ * few 1e-7); for a closed array the weights of a pixel inside it sum to 1.
+ *   normals_host  [n_sensors][3] element normals pointing into the imaged
+ *                 region (normalised here; a zero normal is an error)
+ *   elem_host     [n_sensors] element length (2-D, m) or area (3-D, m^2), >= 0
+ *   omega0        the full angle: 2 pi for a closed curve (2-D), 4 pi for a
+ *                 closed surface, 2 pi for a plane or a hemisphere's half space
+ * A pixel on a sensor has no finite weight.  The handle then reconstructs one
+ * frame per gather launch (pat_bp_reconstruct and the host round trip loop
+ * over frames; pat_bp_preprocess / pat_bp_gather / the no-allocation entry take
+ * one frame per call) and is not accepted by plans or autotuning.  Host mirrors
+ * are updated.  Blocking (synchronises the device).  Errors: PAT_ERR_INVALID
+ * (bad arguments, evicted handle), PAT_ERR_OOM, PAT_ERR_CUDA. */
+pat_status pat_bp_set_solid_angle(pat_bp_t h, const double* normals_host, const double* elem_host,
+                                  double omega0);
+
 /* pat_bp_reconstruct -- the on-line step: Eq. (BP) for n_frames frames that
  * share the handle's table.
  *   signals_dev   [n_frames][n_sensors][n_samples] of dtype; for PAT_BF16 and

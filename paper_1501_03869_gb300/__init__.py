@@ -106,6 +106,21 @@ class BP:
         _lib.check(lib.pat_bp_info(h, ctypes.byref(inf)), "pat_bp_info")
         self.info = {k: getattr(inf, k) for k, _ in _lib.PatInfo._fields_}
 
+    def set_solid_angle(self, normals, elem, omega0):
+        """Exact back projection (Sec. II-C): weight every term by the share of
+        the full angle omega0 that the sensor's element subtends at the pixel,
+        elem_s (n_s . (r - r_s)) / |r - r_s|^d / omega0 (d = grid dimension).
+        normals [ns, 3] point into the imaged region; elem [ns] are element
+        lengths (2-D) or areas (3-D).  Replaces the per-sensor weights; the
+        handle then reconstructs frame by frame and is not accepted by plans."""
+        nrm = np.ascontiguousarray(normals, dtype=np.float64)
+        el = np.ascontiguousarray(elem, dtype=np.float64)
+        if nrm.shape != (self.n_sensors, 3) or el.shape != (self.n_sensors,):
+            raise ValueError("normals must be [ns, 3] and elem [ns]")
+        _lib.check(self._lib.pat_bp_set_solid_angle(self._h, nrm.ctypes.data, el.ctypes.data,
+                                                    float(omega0)), "pat_bp_set_solid_angle")
+        return self
+
     # ------------------------------------------------------------ lifecycle --
     def close(self):
         if getattr(self, "_h", None):

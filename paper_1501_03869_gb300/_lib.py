@@ -25,7 +25,7 @@ EXPORTS = (
     "pat_status_str", "pat_last_error", "pat_bp_create", "pat_bp_reconstruct",
     "pat_bp_preprocess", "pat_bp_gather",
     "pat_bp_reconstruct_host", "pat_bp_reserve", "pat_bp_sync", "pat_bp_info",
-    "pat_bp_table", "pat_bp_destroy", "pat_fmm_host", "pat_fmm_gpu", "pat_table_host",
+    "pat_bp_table", "pat_bp_destroy", "pat_fmm_host", "pat_fmm_gpu", "pat_table_host", "pat_bp_set_solid_angle",
     "pat_test_wait_timeout", "pat_plan_create", "pat_plan_execute", "pat_plan_sync",
     "pat_plan_info", "pat_plan_destroy", "pat_bp_reconstruct_multi", "pat_bp_autotune",
     "pat_bp_evict", "pat_bp_restore", "pat_srv_create", "pat_srv_register", "pat_srv_submit",
@@ -135,6 +135,8 @@ def load():
         lib.pat_fmm_host.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp]
         lib.pat_fmm_gpu.restype = _i
         lib.pat_fmm_gpu.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp]
+        lib.pat_bp_set_solid_angle.restype = _i
+        lib.pat_bp_set_solid_angle.argtypes = [_vp, _vp, _vp, ctypes.c_double]
         lib.pat_table_host.restype = _i
         lib.pat_table_host.argtypes = [_vp, ctypes.POINTER(PatGrid), _vp, _i, _vp, _d, _i, _u,
                                        ctypes.POINTER(PatInfo), _vp, _vp, _vp]

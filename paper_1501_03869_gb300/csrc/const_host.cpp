@@ -27,6 +27,99 @@
 
 namespace patbp {
 
+void tile_nodes(const GridDesc& g, const std::vector<int32_t>& slot_dense, int P, int n_tiles,
+                std::vector<int32_t>& node, std::vector<int32_t>& anchor_node) {
+  node.assign(size_t(n_tiles) * P * 3, 0);
+  anchor_node.assign(size_t(n_tiles) * 3, 0);
+  for (int t = 0; t < n_tiles; ++t) {
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+    for (int p = 0; p < P; ++p) {
+      const int32_t v = slot_dense[size_t(t) * P + p];
+      if (v < 0) continue;
+      int32_t* x = node.data() + (size_t(t) * P + p) * 3;
+      x[0] = int32_t(v % g.n[0]);
+      x[1] = int32_t((v / g.n[0]) % g.n[1]);
+      x[2] = int32_t(int64_t(v) / (int64_t(g.n[0]) * g.n[1]));
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], x[d]);
+        hi[d] = std::max(hi[d], x[d]);
+      }
+    }
+    int32_t* a = anchor_node.data() + size_t(t) * 3;
+    for (int d = 0; d < 3; ++d) a[d] = hi[d] >= 0 ? (lo[d] + hi[d]) / 2 : 0;
+  }
+}
+
+bool build_solid_angle_layout(const GridDesc& g, const std::vector<int32_t>& slot_dense, int P,
+                              int n_tiles, const double* sensors, const double* normals,
+                              const double* elem, int n_sensors, int n_sensors_pad, double omega0,
+                              double unit, bool make_pix, std::vector<float>& wanchor,
+                              std::vector<float>& pix, std::string& err) {
+  if (!(omega0 > 0.0) || !std::isfinite(omega0)) {
+    err = "omega0 must be finite and > 0";
+    return false;
+  }
+  const int nd = g.ndim;
+  std::vector<double> nrm(size_t(n_sensors) * 3, 0.0);
+  for (int s = 0; s < n_sensors; ++s) {
+    double len2 = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      const double c = normals[3 * s + d];
+      if (!std::isfinite(c) || !std::isfinite(sensors[3 * s + d])) {
+        err = "sensor positions and normals must be finite";
+        return false;
+      }
+      len2 += c * c;
+    }
+    if (!(len2 > 0.0)) {
+      err = "sensor " + std::to_string(s) + " has a zero normal";
+      return false;
+    }
+    if (!(elem[s] >= 0.0) || !std::isfinite(elem[s])) {
+      err = "element sizes must be finite and >= 0";
+      return false;
+    }
+    for (int d = 0; d < nd; ++d) nrm[3 * s + d] = normals[3 * s + d] / std::sqrt(len2);
+  }
+  std::vector<int32_t> node, anchor_node;
+  tile_nodes(g, slot_dense, P, n_tiles, node, anchor_node);
+  // w = elem (n . v_m) / |v_m|^d / omega0 with v_m = (dx / unit) v in the
+  // kernel's units: scale = elem / omega0 * (unit / dx)^(d - 1)
+  const double to_unit = unit / g.dx;
+  wanchor.assign(size_t(n_tiles) * n_sensors_pad * 8, 0.0f);
+  for (int t = 0; t < n_tiles; ++t) {
+    const int32_t* a = anchor_node.data() + size_t(t) * 3;
+    for (int s = 0; s < n_sensors; ++s) {
+      float* w = wanchor.data() + (size_t(t) * n_sensors_pad + s) * 8;
+      for (int d = 0; d < nd; ++d) {
+        const double rs = (sensors[3 * s + d] - g.origin[d]) / g.dx;  // node units
+        w[d] = float(unit * (double(a[d]) - rs));
+        w[4 + d] = float(nrm[3 * s + d]);
+      }
+      w[3] = float(elem[s] / omega0 * std::pow(to_unit, double(nd - 1)));
+      w[7] = float(nd);
+    }
+  }
+  if (make_pix) {
+    pix.assign(size_t(n_tiles) * P * 4, 0.0f);
+    for (int t = 0; t < n_tiles; ++t) {
+      const int32_t* a = anchor_node.data() + size_t(t) * 3;
+      for (int p = 0; p < P; ++p) {
+        if (slot_dense[size_t(t) * P + p] < 0) continue;
+        const int32_t* x = node.data() + (size_t(t) * P + p) * 3;
+        double D[3] = {0.0, 0.0, 0.0};
+        for (int d = 0; d < nd; ++d) D[d] = unit * double(x[d] - a[d]);
+        float* q = pix.data() + (size_t(t) * P + p) * 4;
+        q[0] = float(2.0 * D[0]);
+        q[1] = float(2.0 * D[1]);
+        q[2] = float(2.0 * D[2]);
+        q[3] = float(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      }
+    }
+  }
+  return true;
+}
+
 bool build_constant_layout(double c0, const GridDesc& g, const double* sensors, int n_sensors,
                            const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
                            HostTable& out, std::string& err) {
@@ -51,26 +144,12 @@ bool build_constant_layout(double c0, const GridDesc& g, const double* sensors, 
   constexpr double kMargin = 1e-3;
 
   // node coordinates of every slot and the anchor node of every tile
-  std::vector<int32_t> node(size_t(n_tiles) * P * 3, 0);
-  std::vector<int32_t> anchor_node(size_t(n_tiles) * 3, 0);
+  std::vector<int32_t> node, anchor_node;
+  tile_nodes(g, out.slot_dense, P, n_tiles, node, anchor_node);
   std::vector<double> reach(size_t(n_tiles), 0.0);  // max |D| over the tile
   out.pixq.assign(size_t(n_tiles) * P * 4, 0.0f);
   for (int t = 0; t < n_tiles; ++t) {
-    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
-    for (int p = 0; p < P; ++p) {
-      const int32_t v = out.slot_dense[size_t(t) * P + p];
-      if (v < 0) continue;
-      int32_t* x = node.data() + (size_t(t) * P + p) * 3;
-      x[0] = int32_t(v % g.n[0]);
-      x[1] = int32_t((v / g.n[0]) % g.n[1]);
-      x[2] = int32_t(int64_t(v) / (int64_t(g.n[0]) * g.n[1]));
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = std::min(lo[d], x[d]);
-        hi[d] = std::max(hi[d], x[d]);
-      }
-    }
-    int32_t* a = anchor_node.data() + size_t(t) * 3;
-    for (int d = 0; d < 3; ++d) a[d] = hi[d] >= 0 ? (lo[d] + hi[d]) / 2 : 0;
+    const int32_t* a = anchor_node.data() + size_t(t) * 3;
     for (int p = 0; p < P; ++p) {
       if (out.slot_dense[size_t(t) * P + p] < 0) continue;  // padding: the anchor itself
       const int32_t* x = node.data() + (size_t(t) * P + p) * 3;

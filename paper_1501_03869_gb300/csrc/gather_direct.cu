@@ -23,6 +23,12 @@
 // phases are summed in order 0..SW-1 and segments in order 0..n_seg-1.  A frame
 // therefore gives the same bits here as inside any batch that the staged kernel
 // reconstructs.
+//
+// With solid-angle weights (WGT = 1, the exact back projection of Sec. II-C)
+// each term carries its own weight w(pixel, sensor), evaluated here from the
+// sensor's 32-byte weight anchor and the pixel's position terms:
+// acc = fma(m_s, w * lerp, acc).  Only this kernel takes them; handles with
+// such weights reconstruct frame by frame.
 #include <algorithm>
 
 #include "gather.cuh"
@@ -38,6 +44,7 @@ struct DirectParams {
   const float* u;
   const float* anchor;
   const float4* pix;
+  const float* wanchor;
   const int32_t* base;
   const int32_t* slot;
   const int32_t* zero_runs;
@@ -52,9 +59,10 @@ struct DirectParams {
 // sensor's window base in the integrand.  Offsets above `cap` are after the
 // record: they read the zero row `zrow` (a padding row after the record) with
 // phase 0, which adds m * 0 exactly as the staged kernel's zero rows do.
-template <int FMT>
+template <int FMT, int WGT>
 __device__ __forceinline__ void direct_accumulate(float (&acc)[4], const float (&uu)[4], float cap,
-                                                  const uint32_t* row, unsigned zrow, float mm) {
+                                                  const uint32_t* row, unsigned zrow, float mm,
+                                                  const float (&ww)[4]) {
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
     const bool in = uu[x] <= cap;
@@ -62,16 +70,36 @@ __device__ __forceinline__ void direct_accumulate(float (&acc)[4], const float (
     const unsigned i = in ? t : zrow;
     const float ph = in ? uu[x] - float(t) : 0.0f;
     const uint32_t w0 = __ldcg(row + i);
+    float v;
     if constexpr (FMT == kBF32) {
       const float b0 = __uint_as_float(w0), b1 = __uint_as_float(__ldcg(row + i + 1));
-      acc[x] = fmaf(mm, fmaf(ph, b1 - b0, b0), acc[x]);
+      v = fmaf(ph, b1 - b0, b0);
     } else if constexpr (FMT == kBBF16P) {
-      const float v = fmaf(ph, __uint_as_float(w0 & 0xffff0000u), __uint_as_float(w0 << 16));
-      acc[x] = fmaf(mm, v, acc[x]);
+      v = fmaf(ph, __uint_as_float(w0 & 0xffff0000u), __uint_as_float(w0 << 16));
     } else {
       const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&w0));
-      acc[x] = fmaf(mm, fmaf(ph, h.y, h.x), acc[x]);
+      v = fmaf(ph, h.y, h.x);
     }
+    if constexpr (WGT != 0) v = __fmul_rn(ww[x], v);
+    acc[x] = fmaf(mm, v, acc[x]);
+  }
+}
+
+// Solid-angle weights of the lane's 4 pixels for one sensor (exact back
+// projection, Sec. II-C): v = D + e from the pixel terms pq = (2 D, |D|^2) and
+// the sensor's weight anchor E = (e, scale), N = (n, d); w = scale (n . v) /
+// |v|^d, d = 2 or 3 (the same for every sensor of a handle: a uniform branch).
+__device__ __forceinline__ void solid_angle_weights(float (&ww)[4], const float4 (&pq)[4], float4 E,
+                                                    float4 N) {
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const float v0 = fmaf(0.5f, pq[x].x, E.x), v1 = fmaf(0.5f, pq[x].y, E.y),
+                v2 = fmaf(0.5f, pq[x].z, E.z);
+    const float r2 = fmaxf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)), 1.0e-30f);
+    const float nv = fmaf(N.x, v0, fmaf(N.y, v1, N.z * v2));
+    const float y = rsqrtf(r2);
+    const float inv = N.w == 3.0f ? y * y * y : y * y;
+    ww[x] = E.w * (nv * inv);
   }
 }
 
@@ -91,7 +119,7 @@ __device__ __forceinline__ void prefetch_unit(const DirectParams& p, int64_t uni
     bulk_prefetch_l2(p.anchor + (int64_t(tile) * p.n_sensors_pad + s_lo) * 8, uint32_t(n) * 32);
 }
 
-template <int P, int SW, int FMT, int DELAYS>
+template <int P, int SW, int FMT, int DELAYS, int WGT>
 __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
     gather_direct_kernel(const __grid_constant__ DirectParams p) {
   constexpr int PW = P / 128;
@@ -115,27 +143,37 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
     const int seg = int(unit - int64_t(tile) * p.n_seg);
     const int s_lo = seg * p.G, s_hi = min(p.n_sensors, s_lo + p.G);
     float4 pq[4];
-    if constexpr (DELAYS != 0) {
+    if constexpr (DELAYS != 0 || WGT != 0) {
 #pragma unroll
       for (int x = 0; x < 4; ++x) pq[x] = __ldcg(p.pix + int64_t(tile) * P + px0 + x * 32);
     }
+    const float4* wrow = WGT != 0 ? reinterpret_cast<const float4*>(p.wanchor) +
+                                        int64_t(tile) * p.n_sensors_pad * 2
+                                  : nullptr;
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float ww[4] = {1.0f, 1.0f, 1.0f, 1.0f};
     if constexpr (DELAYS == 0) {
       // Table offsets: one sensor at a time, software-pipelined -- the next
       // sensor's offsets and window base are in flight while this one
       // gathers (the first ones before waiting for the preprocessing grid).
       float un[4];
       uint32_t bn = 0u;
+      float4 wn0 = make_float4(0.f, 0.f, 0.f, 0.f), wn1 = wn0;
       auto load_next = [&](int s) {
         bn = uint32_t(__ldcg(p.base + int64_t(tile) * p.n_sensors_pad + s));
         const float* urow = p.u + (int64_t(tile) * p.n_sensors + s) * P + px0;
 #pragma unroll
         for (int x = 0; x < 4; ++x) un[x] = __ldcg(urow + x * 32);
+        if constexpr (WGT != 0) {
+          wn0 = __ldcg(wrow + 2 * s);
+          wn1 = __ldcg(wrow + 2 * s + 1);
+        }
       };
       if (s_lo + sp < s_hi) load_next(s_lo + sp);
       for (int s = s_lo + sp; s < s_hi; s += SW) {
         const float uu[4] = {un[0], un[1], un[2], un[3]};
         const unsigned bs = bn & 0xffffu;
+        if constexpr (WGT != 0) solid_angle_weights(ww, pq, wn0, wn1);
         if (s + SW < s_hi) load_next(s + SW);
         if (!waited) {
           // integrand and multipliers come from the preprocessing grid
@@ -144,7 +182,7 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
         }
         const float mm = __ldcg(p.m + s);
         const uint32_t* row = bsrc + int64_t(s) * p.n_t_pad + bs;
-        direct_accumulate<FMT>(acc, uu, 1.0e29f, row, unsigned(p.n_t_pad - 1) - bs, mm);
+        direct_accumulate<FMT, WGT>(acc, uu, 1.0e29f, row, unsigned(p.n_t_pad - 1) - bs, mm, ww);
       }
     } else {
       // Sensors of this phase in chunks of CH: the loads that do not depend on
@@ -154,6 +192,7 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
         uint32_t bw[CH];
         float uu[CH][4];
         float4 an[DELAYS ? CH : 1][2];
+        float4 wa[WGT ? CH : 1][2];
   #pragma unroll
         for (int j = 0; j < CH; ++j) {
           const int s = c0 + j * SW;
@@ -169,6 +208,10 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
             an[j][0] = __ldcg(ap);
             an[j][1] = __ldcg(ap + 1);
             if (!ok) an[j][1].y = -1.0f;  // cap below every offset: nothing to add
+          }
+          if constexpr (WGT != 0) {
+            wa[j][0] = __ldcg(wrow + 2 * (ok ? s : s_lo));
+            wa[j][1] = __ldcg(wrow + 2 * (ok ? s : s_lo) + 1);
           }
         }
         if (!waited) {
@@ -210,7 +253,9 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
           }
           const unsigned bs = bw[j] & 0xffffu;
           const uint32_t* row = bsrc + int64_t(s) * p.n_t_pad + bs;
-          direct_accumulate<FMT>(acc, uu[j], 1.0e29f, row, unsigned(p.n_t_pad - 1) - bs, mm[j]);
+          if constexpr (WGT != 0) solid_angle_weights(ww, pq, wa[j][0], wa[j][1]);
+          direct_accumulate<FMT, WGT>(acc, uu[j], 1.0e29f, row, unsigned(p.n_t_pad - 1) - bs, mm[j],
+                                      ww);
         }
       }
     }
@@ -277,9 +322,9 @@ cudaError_t launch_pdl(K kern, unsigned grid, unsigned threads, const DirectPara
   return cudaLaunchKernelEx(&cfg, kern, dp);
 }
 
-template <int P, int SW, int FMT, int DELAYS>
+template <int P, int SW, int FMT, int DELAYS, int WGT>
 cudaError_t launch_direct_fmt(const DirectParams& dp, int n_sm, cudaStream_t st) {
-  auto kern = gather_direct_kernel<P, SW, FMT, DELAYS>;
+  auto kern = gather_direct_kernel<P, SW, FMT, DELAYS, WGT>;
   const int threads = 32 * (P / 128) * SW;
   static int per_sm = 0;  // resident CTAs per SM (per instantiation, looked up once)
   if (per_sm == 0) {
@@ -297,12 +342,18 @@ cudaError_t launch_direct_fmt(const DirectParams& dp, int n_sm, cudaStream_t st)
   return launch_pdl(direct_reduce_kernel<P, SW>, std::max(rgrid, 1u), 256u, dp, st);
 }
 
+template <int P, int SW, int DELAYS, int WGT>
+cudaError_t launch_direct_w(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
+  if (fmt == kBF32) return launch_direct_fmt<P, SW, kBF32, DELAYS, WGT>(dp, n_sm, st);
+  if (fmt == kBBF16P) return launch_direct_fmt<P, SW, kBBF16P, DELAYS, WGT>(dp, n_sm, st);
+  if (fmt == kBF16P) return launch_direct_fmt<P, SW, kBF16P, DELAYS, WGT>(dp, n_sm, st);
+  return cudaErrorInvalidValue;
+}
+
 template <int P, int SW, int DELAYS>
 cudaError_t launch_direct_t(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
-  if (fmt == kBF32) return launch_direct_fmt<P, SW, kBF32, DELAYS>(dp, n_sm, st);
-  if (fmt == kBBF16P) return launch_direct_fmt<P, SW, kBBF16P, DELAYS>(dp, n_sm, st);
-  if (fmt == kBF16P) return launch_direct_fmt<P, SW, kBF16P, DELAYS>(dp, n_sm, st);
-  return cudaErrorInvalidValue;
+  return dp.wanchor ? launch_direct_w<P, SW, DELAYS, 1>(fmt, dp, n_sm, st)
+                    : launch_direct_w<P, SW, DELAYS, 0>(fmt, dp, n_sm, st);
 }
 
 }  // namespace
@@ -318,6 +369,7 @@ cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc&
   dp.u = d.u;
   dp.anchor = d.anchor;
   dp.pix = d.pix;
+  dp.wanchor = d.wanchor;
   dp.base = d.base;
   dp.slot = d.slot;
   dp.zero_runs = d.zero_runs;

@@ -54,7 +54,13 @@ struct pat_bp_s {
   int tuned_budget_kb[4][3] = {};
   float* d_u = nullptr;               // table offsets (delays == 0)
   float* d_anchor = nullptr;          // per (tile, sensor) anchors (delays == 1)
-  float4* d_pix = nullptr;            // per-pixel terms (delays == 1)
+  float4* d_pix = nullptr;            // per-pixel terms (delays == 1 or wgt)
+  float* d_wanchor = nullptr;         // solid-angle weight anchors (wgt)
+  int wgt = 0;                        // 1: exact back projection (solid-angle weights)
+  // host copies kept for pat_bp_set_solid_angle: sensor positions and the
+  // dense slot map of the pixel layout
+  std::vector<double> sensors_xyz;
+  std::vector<int32_t> slot_dense;
   int32_t* d_base = nullptr;
   int32_t* d_slot = nullptr;
   int32_t* d_zero_runs = nullptr;
@@ -78,9 +84,10 @@ struct pat_bp_s {
   float* d_out = nullptr;
   size_t out_cap = 0;
   // pinned host copy of the device table (PAT_FLAG_HOST_MIRROR): u (or the
-  // anchors), base, slot, zero runs, weights and the per-pixel terms (constant
-  // speed only); lets the device copy be dropped and reloaded
-  static constexpr int kMirrors = 6;
+  // anchors), base, slot, zero runs, weights, the per-pixel terms (constant
+  // speed or solid-angle weights) and the solid-angle weight anchors; lets the
+  // device copy be dropped and reloaded
+  static constexpr int kMirrors = 7;
   void* mirror[kMirrors] = {};
   size_t mirror_bytes[kMirrors] = {};
   bool evicted = false;

@@ -48,7 +48,9 @@ struct PreMultiParams {
 struct InstDesc {
   const float* u;           // [n_tiles][N_s][P] table offsets (stored-table delays)
   const float* anchor;      // [n_tiles][N_s_pad][8] per-sensor anchors (constant-speed delays)
-  const float4* pix;        // [n_tiles][P] pixel terms (2D, |D|^2) (constant-speed delays)
+  const float4* pix;        // [n_tiles][P] pixel terms (2D, |D|^2) (constant-speed delays or
+                            // solid-angle weights)
+  const float* wanchor;     // [n_tiles][N_s_pad][8] solid-angle weight anchors, or NULL
   const int32_t* base;      // [n_tiles][N_s_pad] window base | (window length << 16)
   const int32_t* slot;      // [n_tiles * P] output index, -1 = padding
   const int32_t* zero_runs; // (start, length) pairs of outputs to clear

@@ -84,6 +84,7 @@ static void free_handle(pat_bp_t h) {
   cudaFree(h->d_u);
   cudaFree(h->d_anchor);
   cudaFree(h->d_pix);
+  cudaFree(h->d_wanchor);
   cudaFree(h->d_base);
   cudaFree(h->d_slot);
   cudaFree(h->d_zero_runs);
@@ -153,9 +154,11 @@ static pat_status new_handle(const GridDesc& g, int n_sensors, int n_samples, do
 }
 
 // Upload the built layout and finish the handle (frees it on failure).
-static pat_status finish_create(pat_bp_t h, const HostTable& tab, const float* weights_host,
-                                pat_bp_t* out) {
+static pat_status finish_create(pat_bp_t h, const HostTable& tab, const double* sensors_host,
+                                const float* weights_host, pat_bp_t* out) {
   const int n_sensors = h->ns;
+  h->sensors_xyz.assign(sensors_host, sensors_host + 3 * size_t(n_sensors));
+  h->slot_dense = tab.slot_dense;
   h->n_tiles = tab.n_tiles;
   h->n_pix = tab.n_pix;
   h->W = tab.W;
@@ -263,7 +266,7 @@ extern "C" pat_status pat_bp_create(const float* speed_host, const pat_grid* gri
     free_handle(h);
     return fail(PAT_ERR_INVALID, err);
   }
-  return finish_create(h, tab, weights_host, out);
+  return finish_create(h, tab, sensors_host, weights_host, out);
 }
 
 extern "C" pat_status pat_bp_create_constant(double c0, const pat_grid* grid,
@@ -288,7 +291,63 @@ extern "C" pat_status pat_bp_create_constant(double c0, const pat_grid* grid,
     free_handle(h);
     return fail(PAT_ERR_INVALID, err);
   }
-  return finish_create(h, tab, weights_host, out);
+  return finish_create(h, tab, sensors_host, weights_host, out);
+}
+
+extern "C" pat_status pat_bp_set_solid_angle(pat_bp_t h, const double* normals_host,
+                                             const double* elem_host, double omega0) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  if (!normals_host || !elem_host) return fail(PAT_ERR_INVALID, "normals or elements NULL");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (h->evicted) return fail(PAT_ERR_INVALID, "the handle's table is evicted (pat_bp_restore)");
+  PAT_CUDA(cudaSetDevice(h->device));
+  // the constant-speed handle's pixel terms are in units of kappa = dx / (c0 dt)
+  const double unit = h->delays ? h->g.dx / (h->c0 * h->dt) : 1.0;
+  std::vector<float> wanchor, pix;
+  std::string err;
+  if (!build_solid_angle_layout(h->g, h->slot_dense, h->P, h->n_tiles, h->sensors_xyz.data(),
+                                normals_host, elem_host, h->ns, h->ns_pad, omega0, unit, !h->delays,
+                                wanchor, pix, err))
+    return fail(PAT_ERR_INVALID, err);
+  PAT_CUDA(cudaDeviceSynchronize());  // no launch of this handle may still read the old buffers
+  const std::vector<float> ones(size_t(h->ns), 1.0f);
+  float* d_wa = nullptr;
+  float4* d_px = nullptr;
+  if (cudaMalloc(&d_wa, wanchor.size() * 4) != cudaSuccess ||
+      (!h->delays && cudaMalloc(&d_px, pix.size() * 4) != cudaSuccess)) {
+    cudaFree(d_wa);
+    return fail(PAT_ERR_OOM, "solid-angle weights");
+  }
+  PAT_CUDA(cudaMemcpy(d_wa, wanchor.data(), wanchor.size() * 4, cudaMemcpyHostToDevice));
+  if (d_px) PAT_CUDA(cudaMemcpy(d_px, pix.data(), pix.size() * 4, cudaMemcpyHostToDevice));
+  // the solid angle replaces the per-sensor weights
+  PAT_CUDA(cudaMemcpy(h->d_w, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice));
+  cudaFree(h->d_wanchor);
+  h->d_wanchor = d_wa;
+  if (d_px) {
+    cudaFree(h->d_pix);
+    h->d_pix = d_px;
+  }
+  h->wgt = 1;
+  if (h->mirror[0]) {  // keep the host mirror complete: weights, pixel terms, anchors
+    std::memcpy(h->mirror[4], ones.data(), ones.size() * 4);
+    const std::vector<float>* src[2] = {&pix, &wanchor};
+    for (int k = 0; k < 2; ++k) {
+      const int i = 5 + k;
+      if (k == 0 && h->delays) continue;  // the constant-speed pixel terms are unchanged
+      const size_t bytes = src[k]->size() * 4;
+      if (h->mirror_bytes[i] != bytes) {
+        cudaFreeHost(h->mirror[i]);
+        h->mirror[i] = nullptr;
+        h->mirror_bytes[i] = 0;
+        if (cudaMallocHost(&h->mirror[i], bytes) != cudaSuccess)
+          return fail(PAT_ERR_OOM, "pinned host mirror");
+        h->mirror_bytes[i] = bytes;
+      }
+      std::memcpy(h->mirror[i], src[k]->data(), bytes);
+    }
+  }
+  return PAT_OK;
 }
 
 namespace patbp {
@@ -380,7 +439,7 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
 // frames share a unit.  No choice here changes the summation order.
 GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst) {
   const size_t limit = size_t(h->max_smem);
-  if (n_frames == 1 && !(h->flags & PAT_FLAG_STAGED_SINGLE)) {
+  if (h->wgt || (n_frames == 1 && !(h->flags & PAT_FLAG_STAGED_SINGLE))) {
     // one frame: the unstaged kernels (same arithmetic and order as the
     // staged kernel with one frame per unit)
     GatherConfig c = config_for(h, 1, 16, 72 * 1024, wst);
@@ -426,6 +485,7 @@ InstDesc make_desc(pat_bp_t h, float* out, int n_frames, int FB, int wst) {
   d.u = h->d_u;
   d.anchor = h->d_anchor;
   d.pix = h->d_pix;
+  d.wanchor = h->wgt ? h->d_wanchor : nullptr;
   d.base = h->d_base;
   d.slot = h->d_slot;
   d.zero_runs = h->d_zero_runs;
@@ -473,8 +533,9 @@ namespace patbp {
 
 // device bytes of the delay data: table offsets, or anchors and pixel terms
 static size_t delay_bytes(pat_bp_t h) {
-  if (h->delays) return size_t(h->n_tiles) * h->ns_pad * 32 + size_t(h->n_tiles) * h->P * 16;
-  return size_t(h->n_tiles) * h->ns * h->P * 4;
+  const size_t wgt = h->wgt ? size_t(h->n_tiles) * h->ns_pad * 32 : 0;
+  if (h->delays) return size_t(h->n_tiles) * h->ns_pad * 32 + size_t(h->n_tiles) * h->P * 16 + wgt;
+  return size_t(h->n_tiles) * h->ns * h->P * 4 + (h->wgt ? size_t(h->n_tiles) * h->P * 16 : 0) + wgt;
 }
 
 size_t table_device_bytes(pat_bp_t h) {
@@ -492,8 +553,9 @@ pat_status evict_locked(pat_bp_t h) {
   if (!h->mirror[0]) return fail(PAT_ERR_INVALID, "eviction needs PAT_FLAG_HOST_MIRROR");
   if (h->evicted) return PAT_OK;
   PAT_CUDA(cudaDeviceSynchronize());
-  void** dev[11] = {reinterpret_cast<void**>(&h->d_u), reinterpret_cast<void**>(&h->d_anchor),
-                    reinterpret_cast<void**>(&h->d_pix), reinterpret_cast<void**>(&h->d_base),
+  void** dev[12] = {reinterpret_cast<void**>(&h->d_u), reinterpret_cast<void**>(&h->d_anchor),
+                    reinterpret_cast<void**>(&h->d_pix), reinterpret_cast<void**>(&h->d_wanchor),
+                    reinterpret_cast<void**>(&h->d_base),
                     reinterpret_cast<void**>(&h->d_slot), reinterpret_cast<void**>(&h->d_zero_runs),
                     reinterpret_cast<void**>(&h->d_w), &h->d_b, reinterpret_cast<void**>(&h->d_m),
                     reinterpret_cast<void**>(&h->d_part), reinterpret_cast<void**>(&h->d_counter)};
@@ -513,7 +575,7 @@ pat_status restore_locked(pat_bp_t h, cudaStream_t st) {
       h->delays ? reinterpret_cast<void**>(&h->d_anchor) : reinterpret_cast<void**>(&h->d_u),
       reinterpret_cast<void**>(&h->d_base), reinterpret_cast<void**>(&h->d_slot),
       reinterpret_cast<void**>(&h->d_zero_runs), reinterpret_cast<void**>(&h->d_w),
-      reinterpret_cast<void**>(&h->d_pix)};
+      reinterpret_cast<void**>(&h->d_pix), reinterpret_cast<void**>(&h->d_wanchor)};
   for (int i = 0; i < pat_bp_s::kMirrors; ++i) {
     if (!h->mirror[i]) continue;
     if (cudaMalloc(dev[i], h->mirror_bytes[i]) != cudaSuccess) {
@@ -565,6 +627,8 @@ static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dty
   if (dtype != PAT_F32 && dtype != PAT_BF16 && dtype != PAT_F16)
     return fail(PAT_ERR_INVALID, "unknown dtype");
   if (dtype != PAT_F32 && !scales_dev) return fail(PAT_ERR_INVALID, "16-bit signals need scales");
+  if (h->wgt && n_frames != 1)
+    return fail(PAT_ERR_INVALID, "solid-angle weights: one frame per preprocess (pat_bp_reconstruct loops)");
   int wst = 0;
   const int FB = pick_config(h, n_frames, fmt_for(dtype), &wst).FB;
   pat_status st = ensure_buffers_fb(h, n_frames, FB);
@@ -580,6 +644,8 @@ static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dty
 
 static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaStream_t stream) {
   if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
+  if (h->wgt && n_frames != 1)
+    return fail(PAT_ERR_INVALID, "solid-angle weights: one frame per gather (pat_bp_reconstruct loops)");
   if (n_frames < 1 || n_frames != h->pre_frames)
     return fail(PAT_ERR_INVALID, "gather needs the preprocess of the same n_frames first");
   int wst = 0;
@@ -609,6 +675,19 @@ pat_status patbp::reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dt
                                       const float* scales_dev, int n_frames, float* out_dev,
                                       cudaStream_t stream) {
   if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
+  if (h->wgt && n_frames > 1) {
+    // solid-angle weights: the unstaged kernel, one frame at a time
+    if (!signals_dev) return fail(PAT_ERR_INVALID, "signals NULL");
+    const size_t row_bytes = size_t(h->ns) * h->nt * (dtype == PAT_F32 ? 4 : 2);
+    for (int f = 0; f < n_frames; ++f) {
+      const void* sig = static_cast<const char*>(signals_dev) + f * row_bytes;
+      const float* sc = scales_dev ? scales_dev + size_t(f) * h->ns : nullptr;
+      pat_status st = preprocess_locked(h, sig, dtype, sc, 1, stream);
+      if (st == PAT_OK) st = gather_locked(h, 1, out_dev + f * h->out_stride, stream);
+      if (st != PAT_OK) return st;
+    }
+    return PAT_OK;
+  }
   pat_status st = preprocess_locked(h, signals_dev, dtype, scales_dev, n_frames, stream);
   if (st != PAT_OK) return st;
   return gather_locked(h, n_frames, out_dev, stream);

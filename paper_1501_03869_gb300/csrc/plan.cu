@@ -348,6 +348,9 @@ static pat_status plan_new(const pat_bp_t* handles, const int* n_frames, int n, 
     if (handles[i]->delays != handles[0]->delays)
       return fail(PAT_ERR_INVALID,
                   "plan handles must share the delay source (stored table or constant speed)");
+    if (handles[i]->wgt)
+      return fail(PAT_ERR_INVALID,
+                  "a handle with solid-angle weights reconstructs on its own (pat_bp_reconstruct)");
   }
   std::unique_ptr<pat_plan_s> pl(new (std::nothrow) pat_plan_s());
   if (!pl) return fail(PAT_ERR_OOM, "plan");

@@ -138,4 +138,27 @@ bool build_constant_layout(double c0, const GridDesc& g, const double* sensors, 
                            const uint8_t* mask, double dt, int n_samples, int P, bool compact_out,
                            HostTable& out, std::string& err);
 
+// Node coordinates of every tile slot ([n_tiles * P][3], padding slots 0) and
+// every tile's anchor node (the centre of its pixels' bounding box, rounded
+// down), the reference point of the per-pixel terms.
+void tile_nodes(const GridDesc& g, const std::vector<int32_t>& slot_dense, int P, int n_tiles,
+                std::vector<int32_t>& node, std::vector<int32_t>& anchor_node);
+
+// Weights of the exact back projection (the solid angle of sensor s's element
+// at pixel r over omega0, Sec. II-C): w = elem_s (n_s . (r - r_s)) /
+// |r - r_s|^d / omega0, d = ndim (2-D: plane angle, x and y only).  The
+// kernels evaluate it from a per-(tile, sensor) anchor [n_tiles][ns_pad][8] =
+// (e.xyz, scale, n.xyz, d), e = unit (r0 - r_s) in node units times `unit`,
+// and the per-pixel terms (2 D, |D|^2), D = unit (r - r0), as v = D + e:
+// w = scale (n . v) / |v|^d with scale = elem / omega0 (unit / dx)^(d - 1).
+// `unit` is the scale of the handle's existing per-pixel terms (the constant-
+// speed kappa) or 1 when the layout makes them (make_pix).  Normals are
+// normalised here; errors (zero normal, negative element, omega0 <= 0) return
+// false with a message.
+bool build_solid_angle_layout(const GridDesc& g, const std::vector<int32_t>& slot_dense, int P,
+                              int n_tiles, const double* sensors, const double* normals,
+                              const double* elem, int n_sensors, int n_sensors_pad, double omega0,
+                              double unit, bool make_pix, std::vector<float>& wanchor,
+                              std::vector<float>& pix, std::string& err);
+
 }  // namespace patbp
