@@ -155,12 +155,12 @@ pat_status pat_bp_create_constant(double c0, const pat_grid* grid, const double*
  *   elem_host     [n_sensors] element length (2-D, m) or area (3-D, m^2), >= 0
  *   omega0        the full angle: 2 pi for a closed curve (2-D), 4 pi for a
  *                 closed surface, 2 pi for a plane or a hemisphere's half space
- * A pixel on a sensor has no finite weight.  The handle then reconstructs one
- * frame per gather launch (pat_bp_reconstruct and the host round trip loop
- * over frames; pat_bp_preprocess / pat_bp_gather / the no-allocation entry take
- * one frame per call) and is not accepted by plans or autotuning.  Host mirrors
- * are updated.  Blocking (synchronises the device).  Errors: PAT_ERR_INVALID
- * (bad arguments, evicted handle), PAT_ERR_OOM, PAT_ERR_CUDA. */
+ * A pixel on a sensor has no finite weight.  Every reconstruction path takes
+ * the handle (single frames, batches, plans whose handles all have weights,
+ * serving, the no-allocation entry); a frame has the same bits alone and in a
+ * batch.  Host mirrors are updated.  Blocking (synchronises the device).
+ * Errors: PAT_ERR_INVALID (bad arguments, evicted handle), PAT_ERR_OOM,
+ * PAT_ERR_CUDA. */
 pat_status pat_bp_set_solid_angle(pat_bp_t h, const double* normals_host, const double* elem_host,
                                   double omega0);
 

@@ -111,8 +111,8 @@ class BP:
         the full angle omega0 that the sensor's element subtends at the pixel,
         elem_s (n_s . (r - r_s)) / |r - r_s|^d / omega0 (d = grid dimension).
         normals [ns, 3] point into the imaged region; elem [ns] are element
-        lengths (2-D) or areas (3-D).  Replaces the per-sensor weights; the
-        handle then reconstructs frame by frame and is not accepted by plans."""
+        lengths (2-D) or areas (3-D).  Replaces the per-sensor weights; plans
+        take the handle together with other weighted handles only."""
         nrm = np.ascontiguousarray(normals, dtype=np.float64)
         el = np.ascontiguousarray(elem, dtype=np.float64)
         if nrm.shape != (self.n_sensors, 3) or el.shape != (self.n_sensors,):

@@ -56,14 +56,35 @@ __device__ __forceinline__ void load_words(const uint32_t* src, uint32_t (&w)[N]
 // the zero rows' values is zero.
 constexpr float kFarOffset = 1.0e30f;
 
+// Solid-angle weights of a lane's 4 pixels for one sensor (the exact back
+// projection that Eq. (BP) approximates, Sec. II-C): v = D + e from the pixel
+// terms pq = (2 D, |D|^2) and the sensor's weight anchor E = (e, scale),
+// N = (n, d); w = scale (n . v) / |v|^d, d = 2 or 3 (the same for every sensor
+// of a handle: a uniform branch).  Both gathers use this function, so a frame
+// gets the same weights alone and in a batch.
+__device__ __forceinline__ void solid_angle_weights(float (&ww)[4], const float4 (&pq)[4], float4 E,
+                                                    float4 N) {
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const float v0 = fmaf(0.5f, pq[x].x, E.x), v1 = fmaf(0.5f, pq[x].y, E.y),
+                v2 = fmaf(0.5f, pq[x].z, E.z);
+    const float r2 = fmaxf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)), 1.0e-30f);
+    const float nv = fmaf(N.x, v0, fmaf(N.y, v1, N.z * v2));
+    const float y = rsqrtf(r2);
+    const float inv = N.w == 3.0f ? y * y * y : y * y;
+    ww[x] = E.w * (nv * inv);
+  }
+}
+
 // Interpolate one sensor's integrand at the lane's 4 window offsets uu (rows
 // from the start of the sensor's window at `off`) and accumulate FB frames
-// weighted by the multipliers sm.  Offsets past the stage's windows read the
+// weighted by the multipliers sm (and, WGT = 1, by the per-pixel weights ww:
+// acc = fma(m, w * lerp, acc)).  Offsets past the stage's windows read the
 // zero rows.
-template <int FB, int FMT>
+template <int FB, int FMT, int WGT>
 __device__ __forceinline__ void lerp_accumulate(float (&acc)[FB][4], const float (&uu)[4],
-                                                const uint32_t* sm, int off, const uint32_t* sw,
-                                                int Wst) {
+                                                const float (&ww)[4], const uint32_t* sm, int off,
+                                                const uint32_t* sw, int Wst) {
   const unsigned lim = unsigned(Wst - off);
   float mm[FB];
   {
@@ -85,32 +106,41 @@ __device__ __forceinline__ void lerp_accumulate(float (&acc)[FB][4], const float
 #pragma unroll
       for (int fb = 0; fb < FB; ++fb) {
         const float b0 = __uint_as_float(w0[fb]), b1 = __uint_as_float(w1[fb]);
-        acc[fb][x] = fmaf(mm[fb], fmaf(ph, b1 - b0, b0), acc[fb][x]);
+        float v = fmaf(ph, b1 - b0, b0);
+        if constexpr (WGT != 0) v = __fmul_rn(ww[x], v);
+        acc[fb][x] = fmaf(mm[fb], v, acc[fb][x]);
       }
     } else if constexpr (FMT == kBBF16P) {
 #pragma unroll
       for (int fb = 0; fb < FB; ++fb) {
-        const float v = fmaf(ph, __uint_as_float(w0[fb] & 0xffff0000u), __uint_as_float(w0[fb] << 16));
+        float v = fmaf(ph, __uint_as_float(w0[fb] & 0xffff0000u), __uint_as_float(w0[fb] << 16));
+        if constexpr (WGT != 0) v = __fmul_rn(ww[x], v);
         acc[fb][x] = fmaf(mm[fb], v, acc[fb][x]);
       }
     } else {
 #pragma unroll
       for (int fb = 0; fb < FB; ++fb) {
         const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&w0[fb]));
-        acc[fb][x] = fmaf(mm[fb], fmaf(ph, h.y, h.x), acc[fb][x]);
+        float v = fmaf(ph, h.y, h.x);
+        if constexpr (WGT != 0) v = __fmul_rn(ww[x], v);
+        acc[fb][x] = fmaf(mm[fb], v, acc[fb][x]);
       }
     }
   }
 }
 
-// One sensor of a stage, delays from the stored table: u[sl][P] in shared memory.
-template <int P, int FB, int FMT>
+// One sensor of a stage, delays from the stored table: u[sl][P] in shared
+// memory; with WGT the sensor's weight anchor is swa[2 sl], swa[2 sl + 1].
+template <int P, int FB, int FMT, int WGT>
 __device__ __forceinline__ void gather_sensor(float (&acc)[FB][4], const float* su, const uint32_t* sm,
-                                              const int* soff, const uint32_t* sw, int sl, int Wst) {
+                                              const int* soff, const uint32_t* sw, int sl, int Wst,
+                                              const float4 (&pq)[4], const float4* swa) {
   float uu[4];
 #pragma unroll
   for (int x = 0; x < 4; ++x) uu[x] = su[sl * P + x * 32];
-  lerp_accumulate<FB, FMT>(acc, uu, sm + sl * FB, soff[sl], sw, Wst);
+  float ww[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+  if constexpr (WGT != 0) solid_angle_weights(ww, pq, swa[2 * sl], swa[2 * sl + 1]);
+  lerp_accumulate<FB, FMT, WGT>(acc, uu, ww, sm + sl * FB, soff[sl], sw, Wst);
 }
 
 // One sensor of a stage, constant-speed delays computed here (Sec. II-C: the
@@ -130,11 +160,11 @@ __device__ __forceinline__ void gather_sensor(float (&acc)[FB][4], const float* 
 // Anchor of the sensor (two float4): (e.x, e.y, e.z, u0), (u0 - base, cap,
 // u0^2, flag), cap = (N_t - 1) - base; offsets above cap are after the
 // record.  Per pixel (registers): pq = (2 D.x, 2 D.y, 2 D.z, |D|^2).
-template <int FB, int FMT>
+template <int FB, int FMT, int WGT>
 __device__ __forceinline__ void gather_sensor_const(float (&acc)[FB][4], const float4 (&pq)[4],
                                                     const float4* sa, const uint32_t* sm,
                                                     const int* soff, const uint32_t* sw, int sl,
-                                                    int Wst) {
+                                                    int Wst, const float4* swa) {
   const float4 A = sa[2 * sl], B = sa[2 * sl + 1];
   float uu[4];
   if (B.w == 0.0f) {  // the same sensor for the whole warp: a uniform branch
@@ -159,22 +189,27 @@ __device__ __forceinline__ void gather_sensor_const(float (&acc)[FB][4], const f
       uu[x] = v > B.y ? kFarOffset : fmaxf(v, 0.0f);
     }
   }
-  lerp_accumulate<FB, FMT>(acc, uu, sm + sl * FB, soff[sl], sw, Wst);
+  float ww[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+  if constexpr (WGT != 0) solid_angle_weights(ww, pq, swa[2 * sl], swa[2 * sl + 1]);
+  lerp_accumulate<FB, FMT, WGT>(acc, uu, ww, sm + sl * FB, soff[sl], sw, Wst);
 }
 
-// Shared-memory layout of one pipeline stage (byte offsets):
+// Shared-memory layout of one pipeline stage (byte offsets); `mode` is the
+// kernel's: bit 0 constant-speed delays, bit 1 solid-angle weights.
 //   u    [S][P] float            the tile's table rows of the stage's sensors,
 //                                or [S][8] float anchors (constant speed)
+//   wa   [S][8] float            solid-angle weight anchors (bit 1 only)
 //   m    [S4][FB] float          multipliers w_s * sigma
 //   off  [S4] int                window offset (rows) of each sensor
 //   win  [Wst + 4][FB] words     the stage's windows packed at `off`, then 4
 //                                zero rows that out-of-record pixels read
 struct StageLayout {
-  size_t u, m, off, win, bytes;
-  __host__ __device__ StageLayout(int S, int P, int FB, int Wst, int delays) {
+  size_t u, wa, m, off, win, bytes;
+  __host__ __device__ StageLayout(int S, int P, int FB, int Wst, int mode) {
     const int S4 = (S + 3) & ~3;
     u = 0;
-    m = u + (delays ? size_t(S) * 32 : size_t(S) * P * 4);
+    wa = u + ((mode & 1) ? size_t(S) * 32 : size_t(S) * P * 4);
+    m = wa + ((mode & 2) ? size_t(S) * 32 : 0);
     off = m + size_t(S4) * FB * 4;
     win = off + size_t(S4) * 4;
     bytes = win + size_t(Wst + 4) * FB * 4;
@@ -210,13 +245,16 @@ constexpr int kRing = 16;  // unit indices in flight between the producer and th
 // Units are handed out by an atomic ticket (sched[0]); the last CTA to finish
 // resets the tickets (sched[1] counts finished CTAs), so a launch -- or a
 // replay of a captured graph -- always starts from zero.
-// DELAYS: 0 = offsets from the stored table (u block per stage), 1 =
-// constant-speed delays computed by the consumers (an anchor per sensor).  The
-// computed delays hold more live registers; the minimum of resident CTAs keeps
-// the compiler from spilling them (0 leaves the table variants unconstrained).
-template <int P, int FB, int FMT, int SW, int DELAYS>
-__global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), DELAYS ? (FB == 1 ? 3 : 2) : 0)
+// MODE bit 0 (DELAYS): 0 = offsets from the stored table (u block per stage),
+// 1 = constant-speed delays computed by the consumers (an anchor per sensor).
+// MODE bit 1 (WGT): solid-angle weights per (pixel, sensor), from a weight
+// anchor per sensor copied into each stage and the pixel terms.  The computed
+// delays hold more live registers; the minimum of resident CTAs keeps the
+// compiler from spilling them (0 leaves the table variants unconstrained).
+template <int P, int FB, int FMT, int SW, int MODE>
+__global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB == 1 ? 3 : 2) : 0)
     gather_kernel(const __grid_constant__ StreamParams p) {
+  constexpr int DELAYS = MODE & 1, WGT = (MODE >> 1) & 1;
   constexpr int PW = P / 128;   // warps across the tile's pixels
   constexpr int NWC = PW * SW;  // consumer warps
   extern __shared__ __align__(128) unsigned char smem[];
@@ -227,7 +265,7 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), DELAYS ? (FB == 1 ?
   int64_t* red_unit = unit_ring + kRing;                           // [2]
   volatile int* abort_flag = reinterpret_cast<volatile int*>(red_unit + 2);
   int* meta = reinterpret_cast<int*>(smem + kHeaderBytes);  // [2][kMaxG] packed bases
-  const StageLayout L(p.S, P, FB, p.Wst, DELAYS);
+  const StageLayout L(p.S, P, FB, p.Wst, MODE);
   unsigned char* stage0 = smem + kHeaderBytes + kMetaBytes;
   float* red = reinterpret_cast<float*>(stage0 + L.bytes * p.stages);  // [2][SW][FB][P]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -316,12 +354,16 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), DELAYS ? (FB == 1 ?
         if (lane < S4) reinterpret_cast<int*>(sb + L.off)[lane] = lane < se ? off : 0;
         __syncwarp();
         const uint32_t dbytes = DELAYS ? uint32_t(se) * 32 : uint32_t(se) * P * 4;
-        const uint32_t bytes = dbytes + uint32_t(se4) * FB * 4 + wrows * FB * 4;
+        const uint32_t wbytes = WGT ? uint32_t(se) * 32 : 0u;
+        const uint32_t bytes = dbytes + wbytes + uint32_t(se4) * FB * 4 + wrows * FB * 4;
         if (lane == 0) {
           mbar_arrive_expect_tx(&full[st], bytes);
           const float* src = DELAYS ? d.anchor + (int64_t(q.tile) * d.n_sensors_pad + s0) * 8
                                     : d.u + (int64_t(q.tile) * d.n_sensors + s0) * P;
           bulk_g2s(sb + L.u, src, dbytes, &full[st]);
+          if (WGT)
+            bulk_g2s(sb + L.wa, d.wanchor + (int64_t(q.tile) * d.n_sensors_pad + s0) * 8, wbytes,
+                     &full[st]);
         }
       }
       if (part & 2) {
@@ -430,8 +472,8 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), DELAYS ? (FB == 1 ?
       const int64_t u = unit_ring[j % kRing];
       if (u < 0) break;
       const UnitPos q = decode_unit(p, u, inst);
-      float4 pq[4];  // constant speed: the lane's pixels relative to the tile anchor
-      if constexpr (DELAYS != 0) {
+      float4 pq[4];  // constant speed or weights: the lane's pixels relative to the tile anchor
+      if constexpr (DELAYS != 0 || WGT != 0) {
         const float4* src = p.inst[q.inst].pix + int64_t(q.tile) * P + pg * 128 + lane;
 #pragma unroll
         for (int x = 0; x < 4; ++x) pq[x] = __ldcg(src + x * 32);
@@ -453,20 +495,21 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), DELAYS ? (FB == 1 ?
         const uint32_t* sm = reinterpret_cast<const uint32_t*>(sb + L.m);
         const int* soff = reinterpret_cast<const int*>(sb + L.off);
         const uint32_t* sw = reinterpret_cast<const uint32_t*>(sb + L.win);
+        const float4* swa = reinterpret_cast<const float4*>(sb + L.wa);
         int sl = sp;
         if constexpr (DELAYS == 0) {
           for (; sl + SW < se; sl += 2 * SW) {
-            gather_sensor<P, FB, FMT>(acc, su, sm, soff, sw, sl, p.Wst);
-            gather_sensor<P, FB, FMT>(acc, su, sm, soff, sw, sl + SW, p.Wst);
+            gather_sensor<P, FB, FMT, WGT>(acc, su, sm, soff, sw, sl, p.Wst, pq, swa);
+            gather_sensor<P, FB, FMT, WGT>(acc, su, sm, soff, sw, sl + SW, p.Wst, pq, swa);
           }
-          if (sl < se) gather_sensor<P, FB, FMT>(acc, su, sm, soff, sw, sl, p.Wst);
+          if (sl < se) gather_sensor<P, FB, FMT, WGT>(acc, su, sm, soff, sw, sl, p.Wst, pq, swa);
         } else {
           const float4* sa = reinterpret_cast<const float4*>(sb + L.u);
           for (; sl + SW < se; sl += 2 * SW) {
-            gather_sensor_const<FB, FMT>(acc, pq, sa, sm, soff, sw, sl, p.Wst);
-            gather_sensor_const<FB, FMT>(acc, pq, sa, sm, soff, sw, sl + SW, p.Wst);
+            gather_sensor_const<FB, FMT, WGT>(acc, pq, sa, sm, soff, sw, sl, p.Wst, swa);
+            gather_sensor_const<FB, FMT, WGT>(acc, pq, sa, sm, soff, sw, sl + SW, p.Wst, swa);
           }
-          if (sl < se) gather_sensor_const<FB, FMT>(acc, pq, sa, sm, soff, sw, sl, p.Wst);
+          if (sl < se) gather_sensor_const<FB, FMT, WGT>(acc, pq, sa, sm, soff, sw, sl, p.Wst, swa);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
@@ -585,10 +628,10 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), DELAYS ? (FB == 1 ?
 }
 
 // ------------------------------------------------------- launch templates --
-template <int P, int FB, int FMT, int SW, int DELAYS>
+template <int P, int FB, int FMT, int SW, int MODE>
 static cudaError_t gather_t(const StreamParams& p, size_t smem, int grid, cudaStream_t st,
                             int* resident, int n_sm) {
-  auto kern = gather_kernel<P, FB, FMT, SW, DELAYS>;
+  auto kern = gather_kernel<P, FB, FMT, SW, MODE>;
   static size_t smem_set = 0;  // largest dynamic smem granted so far (per instantiation)
   if (smem > smem_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -616,66 +659,74 @@ static cudaError_t gather_t(const StreamParams& p, size_t smem, int grid, cudaSt
   return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-template <int P, int FMT, int SW, int DELAYS>
+template <int P, int FMT, int SW, int MODE>
 static cudaError_t gather_fb(int FB, const StreamParams& p, size_t smem, int grid, cudaStream_t st,
                              int* resident, int n_sm) {
   switch (FB) {
-    case 1: return gather_t<P, 1, FMT, SW, DELAYS>(p, smem, grid, st, resident, n_sm);
-    case 2: return gather_t<P, 2, FMT, SW, DELAYS>(p, smem, grid, st, resident, n_sm);
-    case 4: return gather_t<P, 4, FMT, SW, DELAYS>(p, smem, grid, st, resident, n_sm);
-    case 8: return gather_t<P, 8, FMT, SW, DELAYS>(p, smem, grid, st, resident, n_sm);
+    case 1: return gather_t<P, 1, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
+    case 2: return gather_t<P, 2, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
+    case 4: return gather_t<P, 4, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
+    case 8: return gather_t<P, 8, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
     default: return cudaErrorInvalidValue;
   }
 }
 
 // Launch (resident == nullptr) or count resident CTAs of the instantiation
 // that matches the config and the integrand format.
-template <int DELAYS>
+template <int MODE>
 static cudaError_t gather_dispatch_t(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
                                      cudaStream_t st, int* resident, int n_sm) {
   const size_t smem = gather_smem_bytes(c, p.Wst);
   if (c.P == 128 && c.SW == 4) {
-    if (fmt == kBF32) return gather_fb<128, kBF32, 4, DELAYS>(c.FB, p, smem, grid, st, resident, n_sm);
-    if (fmt == kBBF16P) return gather_fb<128, kBBF16P, 4, DELAYS>(c.FB, p, smem, grid, st, resident, n_sm);
-    if (fmt == kBF16P) return gather_fb<128, kBF16P, 4, DELAYS>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBF32) return gather_fb<128, kBF32, 4, MODE>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBBF16P) return gather_fb<128, kBBF16P, 4, MODE>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBF16P) return gather_fb<128, kBF16P, 4, MODE>(c.FB, p, smem, grid, st, resident, n_sm);
   } else if (c.P == 256 && c.SW == 2) {
-    if (fmt == kBF32) return gather_fb<256, kBF32, 2, DELAYS>(c.FB, p, smem, grid, st, resident, n_sm);
-    if (fmt == kBBF16P) return gather_fb<256, kBBF16P, 2, DELAYS>(c.FB, p, smem, grid, st, resident, n_sm);
-    if (fmt == kBF16P) return gather_fb<256, kBF16P, 2, DELAYS>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBF32) return gather_fb<256, kBF32, 2, MODE>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBBF16P) return gather_fb<256, kBBF16P, 2, MODE>(c.FB, p, smem, grid, st, resident, n_sm);
+    if (fmt == kBF16P) return gather_fb<256, kBF16P, 2, MODE>(c.FB, p, smem, grid, st, resident, n_sm);
   }
   return cudaErrorInvalidValue;
 }
 
 // Kernel entry addresses (identify graph nodes when refreshing their parameters).
-template <int P, int FMT, int SW, int DELAYS>
+template <int P, int FMT, int SW, int MODE>
 static const void* gather_func_fb(int FB) {
   switch (FB) {
-    case 1: return reinterpret_cast<const void*>(gather_kernel<P, 1, FMT, SW, DELAYS>);
-    case 2: return reinterpret_cast<const void*>(gather_kernel<P, 2, FMT, SW, DELAYS>);
-    case 4: return reinterpret_cast<const void*>(gather_kernel<P, 4, FMT, SW, DELAYS>);
-    case 8: return reinterpret_cast<const void*>(gather_kernel<P, 8, FMT, SW, DELAYS>);
+    case 1: return reinterpret_cast<const void*>(gather_kernel<P, 1, FMT, SW, MODE>);
+    case 2: return reinterpret_cast<const void*>(gather_kernel<P, 2, FMT, SW, MODE>);
+    case 4: return reinterpret_cast<const void*>(gather_kernel<P, 4, FMT, SW, MODE>);
+    case 8: return reinterpret_cast<const void*>(gather_kernel<P, 8, FMT, SW, MODE>);
   }
   return nullptr;
 }
 
-template <int DELAYS>
+template <int MODE>
 static const void* gather_func_t(const GatherConfig& c, int fmt) {
   if (c.P == 128 && c.SW == 4) {
-    if (fmt == kBF32) return gather_func_fb<128, kBF32, 4, DELAYS>(c.FB);
-    if (fmt == kBBF16P) return gather_func_fb<128, kBBF16P, 4, DELAYS>(c.FB);
-    if (fmt == kBF16P) return gather_func_fb<128, kBF16P, 4, DELAYS>(c.FB);
+    if (fmt == kBF32) return gather_func_fb<128, kBF32, 4, MODE>(c.FB);
+    if (fmt == kBBF16P) return gather_func_fb<128, kBBF16P, 4, MODE>(c.FB);
+    if (fmt == kBF16P) return gather_func_fb<128, kBF16P, 4, MODE>(c.FB);
   } else if (c.P == 256 && c.SW == 2) {
-    if (fmt == kBF32) return gather_func_fb<256, kBF32, 2, DELAYS>(c.FB);
-    if (fmt == kBBF16P) return gather_func_fb<256, kBBF16P, 2, DELAYS>(c.FB);
-    if (fmt == kBF16P) return gather_func_fb<256, kBF16P, 2, DELAYS>(c.FB);
+    if (fmt == kBF32) return gather_func_fb<256, kBF32, 2, MODE>(c.FB);
+    if (fmt == kBBF16P) return gather_func_fb<256, kBBF16P, 2, MODE>(c.FB);
+    if (fmt == kBF16P) return gather_func_fb<256, kBF16P, 2, MODE>(c.FB);
   }
   return nullptr;
 }
 
-// The constant-speed instantiations live in their own translation unit
-// (gather_const.cu) so the two families compile in parallel.
+// The other modes' instantiations live in their own translation units so the
+// families compile in parallel: constant-speed delays (gather_const.cu, mode
+// 1), solid-angle weights with table or constant-speed delays (gather_wgt.cu,
+// modes 2 and 3).
 cudaError_t gather_dispatch_const(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
                                   cudaStream_t st, int* resident, int n_sm);
 const void* gather_func_const(const GatherConfig& c, int fmt);
+cudaError_t gather_dispatch_wgt(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
+                                cudaStream_t st, int* resident, int n_sm);
+const void* gather_func_wgt(const GatherConfig& c, int fmt);
+cudaError_t gather_dispatch_wgt_const(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
+                                      cudaStream_t st, int* resident, int n_sm);
+const void* gather_func_wgt_const(const GatherConfig& c, int fmt);
 
 }  // namespace patbp

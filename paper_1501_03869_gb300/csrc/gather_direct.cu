@@ -25,10 +25,9 @@
 // reconstructs.
 //
 // With solid-angle weights (WGT = 1, the exact back projection of Sec. II-C)
-// each term carries its own weight w(pixel, sensor), evaluated here from the
-// sensor's 32-byte weight anchor and the pixel's position terms:
-// acc = fma(m_s, w * lerp, acc).  Only this kernel takes them; handles with
-// such weights reconstruct frame by frame.
+// each term carries its own weight w(pixel, sensor), evaluated from the
+// sensor's 32-byte weight anchor and the pixel's position terms by the same
+// function as the staged kernel: acc = fma(m_s, w * lerp, acc).
 #include <algorithm>
 
 #include "gather.cuh"
@@ -82,24 +81,6 @@ __device__ __forceinline__ void direct_accumulate(float (&acc)[4], const float (
     }
     if constexpr (WGT != 0) v = __fmul_rn(ww[x], v);
     acc[x] = fmaf(mm, v, acc[x]);
-  }
-}
-
-// Solid-angle weights of the lane's 4 pixels for one sensor (exact back
-// projection, Sec. II-C): v = D + e from the pixel terms pq = (2 D, |D|^2) and
-// the sensor's weight anchor E = (e, scale), N = (n, d); w = scale (n . v) /
-// |v|^d, d = 2 or 3 (the same for every sensor of a handle: a uniform branch).
-__device__ __forceinline__ void solid_angle_weights(float (&ww)[4], const float4 (&pq)[4], float4 E,
-                                                    float4 N) {
-#pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const float v0 = fmaf(0.5f, pq[x].x, E.x), v1 = fmaf(0.5f, pq[x].y, E.y),
-                v2 = fmaf(0.5f, pq[x].z, E.z);
-    const float r2 = fmaxf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)), 1.0e-30f);
-    const float nv = fmaf(N.x, v0, fmaf(N.y, v1, N.z * v2));
-    const float y = rsqrtf(r2);
-    const float inv = N.w == 3.0f ? y * y * y : y * y;
-    ww[x] = E.w * (nv * inv);
   }
 }
 

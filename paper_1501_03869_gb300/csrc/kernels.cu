@@ -202,7 +202,7 @@ __global__ void wait_probe_kernel(int* status, uint64_t timeout_ns) {
 int gather_threads(const GatherConfig& c) { return 32 * ((c.P / 128) * c.SW + 3); }
 
 size_t gather_smem_bytes(const GatherConfig& c, int Wst) {
-  const StageLayout L(c.S, c.P, c.FB, Wst, c.delays);
+  const StageLayout L(c.S, c.P, c.FB, Wst, c.delays | (c.wgt << 1));
   return size_t(kHeaderBytes) + kMetaBytes + L.bytes * c.stages + 2 * size_t(c.SW) * c.FB * c.P * 4;
 }
 
@@ -257,6 +257,9 @@ cudaError_t launch_preprocess(const PreParams& p, cudaStream_t st) {
 
 static cudaError_t gather_dispatch(const GatherConfig& c, int fmt, const StreamParams& p, int grid,
                                    cudaStream_t st, int* resident, int n_sm) {
+  if (c.wgt)
+    return c.delays ? gather_dispatch_wgt_const(c, fmt, p, grid, st, resident, n_sm)
+                    : gather_dispatch_wgt(c, fmt, p, grid, st, resident, n_sm);
   if (c.delays) return gather_dispatch_const(c, fmt, p, grid, st, resident, n_sm);
   return gather_dispatch_t<0>(c, fmt, p, grid, st, resident, n_sm);
 }
@@ -285,6 +288,7 @@ cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p,
 }
 
 const void* gather_kernel_func(const GatherConfig& c, int fmt) {
+  if (c.wgt) return c.delays ? gather_func_wgt_const(c, fmt) : gather_func_wgt(c, fmt);
   return c.delays ? gather_func_const(c, fmt) : gather_func_t<0>(c, fmt);
 }
 

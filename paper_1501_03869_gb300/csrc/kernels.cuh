@@ -84,6 +84,7 @@ struct GatherConfig {
   int S = 16;       // sensors per stage
   int stages = 4;
   int delays = 0;   // 0 stored table, 1 constant speed computed in the kernel
+  int wgt = 0;      // 1: solid-angle weights per (pixel, sensor)
   int direct = 0;   // 1: single frame through the unstaged kernels (gather_direct.cu)
   int n_sm = 0;     // multiprocessors of the device (sizes the unstaged grid)
 };

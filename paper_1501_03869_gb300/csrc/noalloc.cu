@@ -71,8 +71,6 @@ extern "C" pat_status pat_bp_reconstruct_noalloc(pat_bp_t h, const void* signals
   if (dtype != PAT_F32 && !scales_dev) return fail(PAT_ERR_INVALID, "16-bit signals need scales");
   std::lock_guard<std::mutex> lk(h->mu);
   if (h->evicted) return fail(PAT_ERR_INVALID, "the handle's table is evicted (pat_bp_restore)");
-  if (h->wgt && n_frames != 1)
-    return fail(PAT_ERR_INVALID, "solid-angle weights: one frame per call here");
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   PAT_CUDA(cudaSetDevice(h->device));
   const int fmt = fmt_for(dtype);

@@ -419,6 +419,7 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
   c.P = h->P;
   c.SW = h->SW;
   c.delays = h->delays;
+  c.wgt = h->wgt;
   c.n_sm = h->n_sm;
   c.FB = FB;
   c.S = S;
@@ -439,7 +440,7 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
 // frames share a unit.  No choice here changes the summation order.
 GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst) {
   const size_t limit = size_t(h->max_smem);
-  if (h->wgt || (n_frames == 1 && !(h->flags & PAT_FLAG_STAGED_SINGLE))) {
+  if (n_frames == 1 && !(h->flags & PAT_FLAG_STAGED_SINGLE)) {
     // one frame: the unstaged kernels (same arithmetic and order as the
     // staged kernel with one frame per unit)
     GatherConfig c = config_for(h, 1, 16, 72 * 1024, wst);
@@ -511,7 +512,7 @@ InstDesc make_desc(pat_bp_t h, float* out, int n_frames, int FB, int wst) {
 
 int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm) {
   struct Key {
-    int P, FB, SW, S, stages, fmt, wst, delays;
+    int P, FB, SW, S, stages, fmt, wst, delays, wgt;
   };
   static std::mutex mu;
   static std::vector<std::pair<Key, int>> cache;
@@ -519,11 +520,11 @@ int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm) {
   for (auto& e : cache) {
     const Key& k = e.first;
     if (k.P == c.P && k.FB == c.FB && k.SW == c.SW && k.S == c.S && k.stages == c.stages &&
-        k.fmt == fmt && k.wst == wst && k.delays == c.delays)
+        k.fmt == fmt && k.wst == wst && k.delays == c.delays && k.wgt == c.wgt)
       return e.second;
   }
   const int r = gather_resident_ctas(c, fmt, wst, n_sm);
-  cache.push_back({Key{c.P, c.FB, c.SW, c.S, c.stages, fmt, wst, c.delays}, r});
+  cache.push_back({Key{c.P, c.FB, c.SW, c.S, c.stages, fmt, wst, c.delays, c.wgt}, r});
   return r;
 }
 
@@ -627,8 +628,6 @@ static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dty
   if (dtype != PAT_F32 && dtype != PAT_BF16 && dtype != PAT_F16)
     return fail(PAT_ERR_INVALID, "unknown dtype");
   if (dtype != PAT_F32 && !scales_dev) return fail(PAT_ERR_INVALID, "16-bit signals need scales");
-  if (h->wgt && n_frames != 1)
-    return fail(PAT_ERR_INVALID, "solid-angle weights: one frame per preprocess (pat_bp_reconstruct loops)");
   int wst = 0;
   const int FB = pick_config(h, n_frames, fmt_for(dtype), &wst).FB;
   pat_status st = ensure_buffers_fb(h, n_frames, FB);
@@ -644,8 +643,6 @@ static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dty
 
 static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaStream_t stream) {
   if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
-  if (h->wgt && n_frames != 1)
-    return fail(PAT_ERR_INVALID, "solid-angle weights: one frame per gather (pat_bp_reconstruct loops)");
   if (n_frames < 1 || n_frames != h->pre_frames)
     return fail(PAT_ERR_INVALID, "gather needs the preprocess of the same n_frames first");
   int wst = 0;
@@ -675,19 +672,6 @@ pat_status patbp::reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dt
                                       const float* scales_dev, int n_frames, float* out_dev,
                                       cudaStream_t stream) {
   if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
-  if (h->wgt && n_frames > 1) {
-    // solid-angle weights: the unstaged kernel, one frame at a time
-    if (!signals_dev) return fail(PAT_ERR_INVALID, "signals NULL");
-    const size_t row_bytes = size_t(h->ns) * h->nt * (dtype == PAT_F32 ? 4 : 2);
-    for (int f = 0; f < n_frames; ++f) {
-      const void* sig = static_cast<const char*>(signals_dev) + f * row_bytes;
-      const float* sc = scales_dev ? scales_dev + size_t(f) * h->ns : nullptr;
-      pat_status st = preprocess_locked(h, sig, dtype, sc, 1, stream);
-      if (st == PAT_OK) st = gather_locked(h, 1, out_dev + f * h->out_stride, stream);
-      if (st != PAT_OK) return st;
-    }
-    return PAT_OK;
-  }
   pat_status st = preprocess_locked(h, signals_dev, dtype, scales_dev, n_frames, stream);
   if (st != PAT_OK) return st;
   return gather_locked(h, n_frames, out_dev, stream);

@@ -65,6 +65,7 @@ pat_status plan_shape(pat_plan_t pl, int FB, int S, int budget_kb) {
   c.P = pl->P;
   c.SW = pl->SW;
   c.delays = pl->hs[0]->delays;
+  c.wgt = pl->hs[0]->wgt;
   c.FB = FB;
   c.S = S;
   c.stages = 6;
@@ -348,9 +349,9 @@ static pat_status plan_new(const pat_bp_t* handles, const int* n_frames, int n, 
     if (handles[i]->delays != handles[0]->delays)
       return fail(PAT_ERR_INVALID,
                   "plan handles must share the delay source (stored table or constant speed)");
-    if (handles[i]->wgt)
+    if (handles[i]->wgt != handles[0]->wgt)
       return fail(PAT_ERR_INVALID,
-                  "a handle with solid-angle weights reconstructs on its own (pat_bp_reconstruct)");
+                  "plan handles must all have solid-angle weights or all not (one kernel mode)");
   }
   std::unique_ptr<pat_plan_s> pl(new (std::nothrow) pat_plan_s());
   if (!pl) return fail(PAT_ERR_OOM, "plan");

@@ -9,8 +9,9 @@ Arrays: the paper-shaped ring of C1, a non-circular (elliptical) ring with
 unequal elements on the skull map, and the 3-D hemisphere of the serving
 subject through the constant-speed path.  Tolerances are those of the
 stored-table path (FP32 rel-L2 <= 1e-5 and max-abs <= 1e-4 of the image's
-peak, 16-bit rel-L2 <= 5e-3 on the FP32 signals); frame batching, eviction and
-the no-allocation entry are checked bit for bit.
+peak, 16-bit rel-L2 <= 5e-3 on the FP32 signals); frame batching (the staged
+kernel) against single frames (the unstaged one), plans, eviction and the
+no-allocation entry are checked bit for bit.
 """
 import math
 
@@ -154,23 +155,62 @@ def test_hemisphere_constant_speed_3d():
     check_fp32(img, ref)
 
 
-def test_frames_loop_equals_single_frames_and_noalloc():
-    w = synth.config1(n_frames=3)
+def test_batched_frames_equal_single_frames_bitwise():
+    """Frames in batches take the staged kernel (the weight anchors copied into
+    each stage), single frames the unstaged one; both evaluate the weights with
+    the same function and sum in the same order, so every frame has the same
+    bits alone, in a batch of 3 or 8, through the no-allocation entry, and with
+    PAT_FLAG_STAGED_SINGLE -- for table and constant-speed handles, FP32 and BF16."""
+    w = synth.config1(n_frames=8)
     nrm, elem = ring_geometry(w.sensors)
-    with BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, w.mask) as bp:
-        bp.set_solid_angle(nrm, elem, 2.0 * math.pi)
-        all3 = run(bp, w.signals)
-        for f in range(3):
-            one = run(bp, w.signals[f:f + 1])
-            assert np.array_equal(one[0], all3[f])
-        s = torch.from_numpy(np.ascontiguousarray(w.signals[:1], dtype=np.float32)).cuda()
-        out = torch.empty((1,) + w.speed.shape, dtype=torch.float32, device="cuda")
-        bp.reconstruct_noalloc(s, out=out)
-        bp.sync()
-        assert np.array_equal(out.cpu().numpy()[0].astype(np.float64), all3[0])
+    makers = [lambda fl: BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, w.mask, flags=fl),
+              lambda fl: BP.constant(1560.0, w.speed.shape, w.dx, w.origin, w.sensors, w.dt, w.nt,
+                                     mask=w.mask, flags=fl)]
+    for make in makers:
+        for dtype in ("f32", "bf16"):
+            with make(0) as bp:
+                bp.set_solid_angle(nrm, elem, 2.0 * math.pi)
+                all8 = run(bp, w.signals, dtype)
+                three = run(bp, w.signals[:3], dtype)
+                singles = [run(bp, w.signals[f:f + 1], dtype)[0] for f in range(8)]
+                if dtype == "f32":
+                    s3 = torch.from_numpy(np.ascontiguousarray(w.signals[:3], dtype=np.float32)).cuda()
+                    out = torch.empty((3,) + w.speed.shape, dtype=torch.float32, device="cuda")
+                    bp.reconstruct_noalloc(s3, out=out)
+                    bp.sync()
+                    assert np.array_equal(out.cpu().numpy().astype(np.float64), three)
+            for f in range(8):
+                assert np.array_equal(all8[f], singles[f])
+            for f in range(3):
+                assert np.array_equal(three[f], singles[f])
+            with make(_lib.PAT_FLAG_STAGED_SINGLE) as bp:
+                bp.set_solid_angle(nrm, elem, 2.0 * math.pi)
+                staged1 = run(bp, w.signals[:1], dtype)
+            assert np.array_equal(staged1[0], singles[0])
+
+
+def test_plan_of_weighted_handles_equals_the_handles():
+    w = synth.config1(n_frames=4)
+    sens2, nrm2, elem2 = ellipse_array(80, 60.0 * w.dx, 56.0 * w.dx)
+    nrm, elem = ring_geometry(w.sensors)
+    a = BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, w.mask).set_solid_angle(nrm, elem, 2 * math.pi)
+    b = BP(w.speed, w.dx, w.origin, sens2, w.dt, w.nt, w.mask).set_solid_angle(nrm2, elem2, 2 * math.pi)
+    rng = np.random.default_rng(5)
+    sig_b = rng.standard_normal((2, 80, w.nt)).astype(np.float32)
+    ref_a, ref_b = run(a, w.signals), run(b, sig_b)
+    plan = Plan([a, b], [4, 2])
+    outs = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.out_shapes()]
+    plan.execute([torch.from_numpy(np.ascontiguousarray(w.signals, dtype=np.float32)).cuda(),
+                  torch.from_numpy(sig_b).cuda()], outs)
+    plan.sync()
+    assert np.array_equal(outs[0].cpu().numpy().astype(np.float64), ref_a)
+    assert np.array_equal(outs[1].cpu().numpy().astype(np.float64), ref_b)
+    plan.close()
+    with BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, w.mask) as plain:
         with pytest.raises(PatError):
-            bp.reconstruct_noalloc(torch.from_numpy(np.ascontiguousarray(w.signals, dtype=np.float32)).cuda(),
-                                   out=torch.empty((3,) + w.speed.shape, dtype=torch.float32, device="cuda"))
+            Plan([a, plain], [1, 1])
+    a.close()
+    b.close()
 
 
 def test_eviction_keeps_the_weights():
@@ -186,7 +226,7 @@ def test_eviction_keeps_the_weights():
     assert np.array_equal(a, b)
 
 
-def test_plans_refuse_and_bad_arguments_rejected():
+def test_bad_arguments_rejected():
     w = synth.config1(n_frames=1)
     nrm, elem = ring_geometry(w.sensors)
     with BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, w.mask) as bp:
@@ -196,6 +236,3 @@ def test_plans_refuse_and_bad_arguments_rejected():
             bp.set_solid_angle(nrm, -elem, 2.0 * math.pi)
         with pytest.raises(PatError):
             bp.set_solid_angle(nrm, elem, 0.0)
-        bp.set_solid_angle(nrm, elem, 2.0 * math.pi)
-        with pytest.raises(PatError):
-            Plan([bp], [1])
