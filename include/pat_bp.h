@@ -211,10 +211,13 @@ pat_status pat_bp_reconstruct_noalloc(pat_bp_t h, const void* signals_dev, pat_d
                                       const float* scales_dev, int n_frames, float* out_dev,
                                       pat_stream_t stream);
 
-/* pat_bp_reconstruct_host -- the paper's timed on-line path (Sec. III): copy
- * signals and scales from host memory, reconstruct, copy the image back.
- * Synchronous; uses the handle's own stream and staging buffers.  Pinned host
- * memory gives the fastest copies but is not required. */
+/* pat_bp_reconstruct_host -- the paper's timed on-line path (Sec. III):
+ * signals and scales from host memory in, the image to host memory out.
+ * Synchronous; uses the handle's own stream.  Page-locked (pinned) buffers are
+ * read and written in place by the kernels (the preprocessing reads the
+ * signals across the host link, the last kernel stores the image there), with
+ * no staging copy; pageable buffers are copied through device staging buffers.
+ * The caller must not modify the buffers during the call. */
 pat_status pat_bp_reconstruct_host(pat_bp_t h, const void* signals_host, pat_dtype dtype,
                                    const float* scales_host, int n_frames, float* out_host);
 

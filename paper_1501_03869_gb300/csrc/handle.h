@@ -83,6 +83,8 @@ struct pat_bp_s {
   size_t scales_cap = 0;
   float* d_out = nullptr;
   size_t out_cap = 0;
+  int* host_status = nullptr;         // host-mapped copy of the status word
+  int* host_status_dev = nullptr;     // its device address
   // pinned host copy of the device table (PAT_FLAG_HOST_MIRROR): u (or the
   // anchors), base, slot, zero runs, weights, the per-pixel terms (constant
   // speed or solid-angle weights) and the solid-angle weight anchors; lets the

@@ -183,6 +183,13 @@ __global__ void __launch_bounds__(256) preprocess_multi_kernel(const __grid_cons
 
 
 // ------------------------------------------------------------- wait probe --
+__global__ void status_export_kernel(const int* status, int* host_status) { *host_status = *status; }
+
+cudaError_t launch_status_export(const int* status, int* host_status, cudaStream_t st) {
+  status_export_kernel<<<1, 1, 0, st>>>(status, host_status);
+  return cudaGetLastError();
+}
+
 __global__ void wait_probe_kernel(int* status, uint64_t timeout_ns) {
   __shared__ uint64_t bar;
   if (threadIdx.x == 0) {

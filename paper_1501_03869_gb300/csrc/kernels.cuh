@@ -95,6 +95,10 @@ int gather_threads(const GatherConfig& c);
 int gather_resident_ctas(const GatherConfig& c, int fmt, int Wst, int n_sm);
 
 cudaError_t launch_preprocess(const PreParams& p, cudaStream_t st);
+// Copy the device status word into a host-mapped word (after the stream's
+// earlier work), so the host reads it after a stream synchronisation without
+// a blocking copy.
+cudaError_t launch_status_export(const int* status, int* host_status, cudaStream_t st);
 cudaError_t launch_preprocess_multi(const PreMultiParams& p, cudaStream_t st);
 const void* gather_kernel_func(const GatherConfig& c, int fmt);
 const void* preprocess_multi_func(int dtype, int fmt, int FB);

@@ -99,6 +99,7 @@ static void free_handle(pat_bp_t h) {
   cudaFree(h->d_scales);
   cudaFree(h->d_out);
   for (int i = 0; i < pat_bp_s::kMirrors; ++i) cudaFreeHost(h->mirror[i]);
+  cudaFreeHost(h->host_status);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }
@@ -714,6 +715,17 @@ static pat_status grow(void** p, size_t* cap, size_t need, const char* what) {
   return PAT_OK;
 }
 
+// Device address of a host pointer that the device can access in place
+// (page-locked memory), or nullptr.
+static void* device_address(const void* host_ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host_ptr) != cudaSuccess) {
+    cudaGetLastError();  // not a CUDA-known pointer: clear the error, stage the buffer
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 extern "C" pat_status pat_bp_reconstruct_host(pat_bp_t h, const void* signals_host, pat_dtype dtype,
                                               const float* scales_host, int n_frames,
                                               float* out_host) {
@@ -727,21 +739,45 @@ extern "C" pat_status pat_bp_reconstruct_host(pat_bp_t h, const void* signals_ho
   const size_t sc_bytes = size_t(n_frames) * h->ns * sizeof(float);
   const size_t out_bytes = size_t(n_frames) * h->out_stride * sizeof(float);
   pat_status st;
-  if ((st = grow(&h->d_sig, &h->sig_cap, sig_bytes, "signal staging")) != PAT_OK) return st;
-  if (scales_host &&
-      (st = grow(reinterpret_cast<void**>(&h->d_scales), &h->scales_cap, sc_bytes, "scales")) != PAT_OK)
-    return st;
-  if ((st = grow(reinterpret_cast<void**>(&h->d_out), &h->out_cap, out_bytes, "output staging")) != PAT_OK)
-    return st;
   cudaStream_t s = h->own_stream;
-  PAT_CUDA(cudaMemcpyAsync(h->d_sig, signals_host, sig_bytes, cudaMemcpyHostToDevice, s));
-  if (scales_host) PAT_CUDA(cudaMemcpyAsync(h->d_scales, scales_host, sc_bytes, cudaMemcpyHostToDevice, s));
-  st = reconstruct_locked(h, h->d_sig, dtype, scales_host ? h->d_scales : nullptr, n_frames, h->d_out, s);
+  // Page-locked host buffers are addressable by the device (over NVLink-C2C on
+  // a Grace host): the preprocessing kernel then reads the signals and scales
+  // in place and the last kernel writes the image in place -- no staging
+  // copies.  Pageable buffers go through device staging buffers.
+  const void* sig_dev = device_address(signals_host);
+  const float* sc_dev = scales_host ? static_cast<const float*>(device_address(scales_host)) : nullptr;
+  float* out_dev = static_cast<float*>(device_address(out_host));
+  if (!sig_dev) {
+    if ((st = grow(&h->d_sig, &h->sig_cap, sig_bytes, "signal staging")) != PAT_OK) return st;
+    PAT_CUDA(cudaMemcpyAsync(h->d_sig, signals_host, sig_bytes, cudaMemcpyHostToDevice, s));
+    sig_dev = h->d_sig;
+  }
+  if (scales_host && !sc_dev) {
+    if ((st = grow(reinterpret_cast<void**>(&h->d_scales), &h->scales_cap, sc_bytes, "scales")) != PAT_OK)
+      return st;
+    PAT_CUDA(cudaMemcpyAsync(h->d_scales, scales_host, sc_bytes, cudaMemcpyHostToDevice, s));
+    sc_dev = h->d_scales;
+  }
+  const bool out_staged = out_dev == nullptr;
+  if (out_staged) {
+    if ((st = grow(reinterpret_cast<void**>(&h->d_out), &h->out_cap, out_bytes, "output staging")) != PAT_OK)
+      return st;
+    out_dev = h->d_out;
+  }
+  if (!h->host_status) {
+    if (cudaHostAlloc(&h->host_status, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+      h->host_status = nullptr;
+      return fail(PAT_ERR_OOM, "host status word");
+    }
+    PAT_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->host_status_dev), h->host_status, 0));
+  }
+  *reinterpret_cast<volatile int*>(h->host_status) = 0;
+  st = reconstruct_locked(h, sig_dev, dtype, sc_dev, n_frames, out_dev, s);
   if (st != PAT_OK) return st;
-  PAT_CUDA(cudaMemcpyAsync(out_host, h->d_out, out_bytes, cudaMemcpyDeviceToHost, s));
+  if (out_staged) PAT_CUDA(cudaMemcpyAsync(out_host, out_dev, out_bytes, cudaMemcpyDeviceToHost, s));
+  PAT_CUDA(launch_status_export(h->d_status, h->host_status_dev, s));
   PAT_CUDA(cudaStreamSynchronize(s));
-  int flag = 0;
-  PAT_CUDA(cudaMemcpy(&flag, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  const int flag = *reinterpret_cast<volatile int*>(h->host_status);
   if (flag) {
     cudaMemset(h->d_status, 0, sizeof(int));
     if (h->d_counter) cudaMemset(h->d_counter, 0, h->counter_cap);
