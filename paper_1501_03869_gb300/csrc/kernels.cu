@@ -29,6 +29,40 @@ __device__ __forceinline__ float load_sample(const void* sig, int64_t i) {
   }
 }
 
+// p_k0 .. p_{k0+7} of a row, times sc, zero outside [0, n): one or two 16-byte
+// loads when the run lies in the row and is aligned (so signals read in place
+// from host memory cost few requests), else one load per sample.
+template <int DT>
+__device__ __forceinline__ void load_run8(const void* sig, int64_t row0, int k0, int n, float sc,
+                                          float* v) {
+  const size_t esz = DT == 0 ? 4 : 2;
+  const unsigned char* ptr = static_cast<const unsigned char*>(sig) + (row0 + k0) * int64_t(esz);
+  if (k0 >= 0 && k0 + 8 <= n && (reinterpret_cast<uintptr_t>(ptr) & 15) == 0) {
+    if constexpr (DT == 0) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(ptr));
+      const float4 b = __ldg(reinterpret_cast<const float4*>(ptr) + 1);
+      const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = __fmul_rn(x[j], sc);
+    } else {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(ptr));
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const unsigned short h = (unsigned short)(w[j >> 1] >> ((j & 1) * 16));
+        const float x = DT == 1 ? __bfloat162float(__ushort_as_bfloat16(h)) : __half2float(__ushort_as_half(h));
+        v[j] = __fmul_rn(x, sc);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = k0 + j;
+      v[j] = (k >= 0 && k < n) ? __fmul_rn(load_sample<DT>(sig, row0 + k), sc) : 0.0f;
+    }
+  }
+}
+
 template <int FMT>
 __device__ __forceinline__ uint32_t encode_pair(float v0, float v1) {
   if constexpr (FMT == kBBF16P) {
@@ -57,7 +91,9 @@ __device__ __forceinline__ void store_words(uint32_t* dst, const uint32_t (&w)[N
 
 // One CTA per (sensor, frame group) row; every thread owns K consecutive
 // samples of the row for all FB frames and issues all its loads before any
-// use.  Rows are written frame-interleaved, K * FB words per thread.
+// use; the samples just outside its run (p_{k0-1}, p_{k0+K}, p_{k0+K+1}) come
+// from the neighbouring lanes by shuffles, so the loops run warp-uniformly.
+// Rows are written frame-interleaved, K * FB words per thread.
 template <int DT, int FMT, int FB>
 __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g) {
   constexpr int K = 8;
@@ -76,14 +112,22 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
   }
   // b_{k0..k0+K} of frame fb (K + 1 values; the last feeds the pair slope).
   // Products and differences are explicitly rounded (no contraction into
-  // FMAs): the values do not depend on how the compiler schedules them.
+  // FMAs): the values do not depend on how the compiler schedules them.  All
+  // lanes of a warp call it together (consecutive runs, k0 = lane K + ...).
+  const int lane = threadIdx.x & 31;
+  auto sample = [&](int fb, int k) {
+    return (k >= 0 && k < n) ? __fmul_rn(load_sample<DT>(p.sig, row0[fb] + k), sc[fb]) : 0.0f;
+  };
   auto b_run = [&](int fb, int k0, float (&b)[K + 1]) {
+    static_assert(K == 8, "runs of 8 samples");
     float v[K + 3];  // p_{k0-1} .. p_{k0+K+1}
-#pragma unroll
-    for (int j = 0; j < K + 3; ++j) {
-      const int k = k0 - 1 + j;
-      v[j] = (k >= 0 && k < n) ? __fmul_rn(load_sample<DT>(p.sig, row0[fb] + k), sc[fb]) : 0.0f;
-    }
+    load_run8<DT>(p.sig, row0[fb], k0, n, sc[fb], v + 1);
+    const float prev = __shfl_up_sync(0xffffffffu, v[K], 1);
+    const float nx1 = __shfl_down_sync(0xffffffffu, v[1], 1);
+    const float nx2 = __shfl_down_sync(0xffffffffu, v[2], 1);
+    v[0] = lane == 0 ? sample(fb, k0 - 1) : prev;
+    v[K + 1] = lane == 31 ? sample(fb, k0 + K) : nx1;
+    v[K + 2] = lane == 31 ? sample(fb, k0 + K + 1) : nx2;
 #pragma unroll
     for (int j = 0; j <= K; ++j) {
       const int k = k0 + j;
@@ -102,7 +146,8 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
     float mx[FB];
 #pragma unroll
     for (int fb = 0; fb < FB; ++fb) mx[fb] = 0.0f;
-    for (int k0 = threadIdx.x * K; k0 < n; k0 += blockDim.x * K) {
+    for (int kw = (threadIdx.x & ~31) * K; kw < n; kw += blockDim.x * K) {
+      const int k0 = kw + lane * K;  // runs past the row give b = 0
 #pragma unroll
       for (int fb = 0; fb < FB; ++fb) {
         float b[K + 1];
@@ -128,7 +173,8 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
     }
   }
   uint32_t* dst = static_cast<uint32_t*>(p.b) + (int64_t(g) * p.n_sensors + s) * p.n_t_pad * FB;
-  for (int k0 = threadIdx.x * K; k0 < p.n_t_pad; k0 += blockDim.x * K) {
+  for (int kw = (threadIdx.x & ~31) * K; kw < p.n_t_pad; kw += blockDim.x * K) {
+    const int k0 = kw + lane * K;
     uint32_t w[K * FB];
 #pragma unroll
     for (int fb = 0; fb < FB; ++fb) {
@@ -145,7 +191,7 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
         for (int j = 0; j < K; ++j) w[j * FB + fb] = 0u;
       }
     }
-    store_words<K * FB>(dst + int64_t(k0) * FB, w);
+    if (k0 < p.n_t_pad) store_words<K * FB>(dst + int64_t(k0) * FB, w);
   }
   if (threadIdx.x < FB) {
     const int fb = threadIdx.x;
