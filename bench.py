@@ -498,6 +498,8 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     e2e = {"value": world * updates * len(e2e_t) / sum(e2e_t) / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": int(w.signals.nbytes), "d2h_bytes_per_step": int(out_np.nbytes),
+           "path": "pat_bp_reconstruct_host on page-locked buffers: the kernels read the signals and "
+                   "write the image in host memory over the host link, L2 flushed before every call",
            "ms_per_step": sum(e2e_t) / len(e2e_t) * 1e3,
            "p50_ms": float(np.percentile(e2e_t, 50) * 1e3),
            "p99_ms": float(np.percentile(e2e_t, 99) * 1e3)}
