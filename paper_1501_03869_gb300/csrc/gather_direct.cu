@@ -51,6 +51,8 @@ struct DirectParams {
   const float* m;
   float* out;
   float* part;  // [n_tiles][n_seg][SW][P] phase sums
+  const int* status;
+  int* host_status;  // the reduction copies *status here when set
   int n_zero_runs, n_sensors, n_sensors_pad, n_t_pad, n_tiles, n_seg, G;
 };
 
@@ -259,6 +261,8 @@ __global__ void __launch_bounds__(256) direct_reduce_kernel(const __grid_constan
     for (int i2 = threadIdx.x; i2 < len; i2 += blockDim.x) p.out[st0 + i2] = 0.0f;
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the kernels before this one are complete: their status is final
+  if (p.host_status && blockIdx.x == 0 && threadIdx.x == 0) *p.host_status = __ldcg(p.status);
   const int64_t n = int64_t(p.n_tiles) * P;
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n;
        idx += int64_t(gridDim.x) * blockDim.x) {
@@ -344,7 +348,7 @@ size_t direct_part_floats(const GatherConfig& c, int n_tiles, int n_seg) {
 }
 
 cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc& d, int n_sm,
-                                 cudaStream_t st) {
+                                 const int* status, int* host_status, cudaStream_t st) {
   if (d.n_frames != 1 || c.FB != 1 || d.n_fg != 1 || n_sm < 1 || !d.part) return cudaErrorInvalidValue;
   DirectParams dp;
   dp.u = d.u;
@@ -358,6 +362,8 @@ cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc&
   dp.m = d.m;
   dp.out = d.out;
   dp.part = d.part;
+  dp.status = status;
+  dp.host_status = host_status;
   dp.n_zero_runs = d.n_zero_runs;
   dp.n_sensors = d.n_sensors;
   dp.n_sensors_pad = d.n_sensors_pad;

@@ -118,9 +118,13 @@ size_t resident_bytes(pat_bp_t h);
 size_t table_device_bytes(pat_bp_t h);
 pat_status evict_locked(pat_bp_t h);
 // preprocess + gather on stream (caller holds h->mu or owns h exclusively)
+// With host_status set, the status word ends up there too: *exported tells
+// whether the launches already copied it (the unstaged path), else the caller
+// must.
 pat_status reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
                               const float* scales_dev, int n_frames, float* out_dev,
-                              cudaStream_t stream);
+                              cudaStream_t stream, int* host_status = nullptr,
+                              bool* exported = nullptr);
 pat_status restore_locked(pat_bp_t h, cudaStream_t st);
 // resident gather CTAs for a config (cached per config)
 int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm);

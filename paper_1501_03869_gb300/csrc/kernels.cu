@@ -335,7 +335,7 @@ cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p,
   if (p.n_units == 0) return cudaSuccess;
   if (c.direct) {
     if (p.n_inst != 1) return cudaErrorInvalidValue;
-    return launch_gather_direct(c, fmt, p.inst[0], c.n_sm, st);
+    return launch_gather_direct(c, fmt, p.inst[0], c.n_sm, p.status, p.host_status, st);
   }
   return gather_dispatch(c, fmt, p, grid, st, nullptr, 0);
 }

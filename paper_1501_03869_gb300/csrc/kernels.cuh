@@ -73,6 +73,8 @@ struct StreamParams {
   int stages;               // pipeline depth
   int Wst;                  // window rows one stage can need (max over instances)
   int* status;
+  int* host_status;         // host-mapped word the unstaged path's last kernel copies the
+                            // status into, or NULL
   unsigned* sched;          // [4] zero-initialised: unit ticket (64-bit) and CTAs finished
   uint64_t timeout_ns;
 };
@@ -109,6 +111,7 @@ cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t st)
 // kernel (c.FB == 1; d.part holds direct_part_floats floats); same arithmetic
 // and summation order as the staged kernel with one frame per unit.
 cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc& d, int n_sm,
+                                 const int* status, int* host_status,
                                  cudaStream_t st);
 // Phase sums the unstaged gather stores (floats).
 size_t direct_part_floats(const GatherConfig& c, int n_tiles, int n_seg);

@@ -642,7 +642,8 @@ static pat_status preprocess_locked(pat_bp_t h, const void* signals_dev, pat_dty
   return PAT_OK;
 }
 
-static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaStream_t stream) {
+static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaStream_t stream,
+                                int* host_status = nullptr, bool* exported = nullptr) {
   if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
   if (n_frames < 1 || n_frames != h->pre_frames)
     return fail(PAT_ERR_INVALID, "gather needs the preprocess of the same n_frames first");
@@ -659,6 +660,8 @@ static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaSt
   sp.stages = c.stages;
   sp.Wst = wst;
   sp.status = h->d_status;
+  sp.host_status = c.direct ? host_status : nullptr;
+  if (exported) *exported = c.direct && host_status;
   sp.sched = h->d_sched;
   sp.timeout_ns = 2000000000ull;
   const int res = resident_ctas(c, h->pre_fmt, wst, h->n_sm);
@@ -671,11 +674,12 @@ static pat_status gather_locked(pat_bp_t h, int n_frames, float* out_dev, cudaSt
 
 pat_status patbp::reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
                                       const float* scales_dev, int n_frames, float* out_dev,
-                                      cudaStream_t stream) {
+                                      cudaStream_t stream, int* host_status, bool* exported) {
   if (!out_dev) return fail(PAT_ERR_INVALID, "out NULL");
+  if (exported) *exported = false;
   pat_status st = preprocess_locked(h, signals_dev, dtype, scales_dev, n_frames, stream);
   if (st != PAT_OK) return st;
-  return gather_locked(h, n_frames, out_dev, stream);
+  return gather_locked(h, n_frames, out_dev, stream, host_status, exported);
 }
 
 extern "C" pat_status pat_bp_preprocess(pat_bp_t h, const void* signals_dev, pat_dtype dtype,
@@ -772,10 +776,11 @@ extern "C" pat_status pat_bp_reconstruct_host(pat_bp_t h, const void* signals_ho
     PAT_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->host_status_dev), h->host_status, 0));
   }
   *reinterpret_cast<volatile int*>(h->host_status) = 0;
-  st = reconstruct_locked(h, sig_dev, dtype, sc_dev, n_frames, out_dev, s);
+  bool exported = false;
+  st = reconstruct_locked(h, sig_dev, dtype, sc_dev, n_frames, out_dev, s, h->host_status_dev, &exported);
   if (st != PAT_OK) return st;
   if (out_staged) PAT_CUDA(cudaMemcpyAsync(out_host, out_dev, out_bytes, cudaMemcpyDeviceToHost, s));
-  PAT_CUDA(launch_status_export(h->d_status, h->host_status_dev, s));
+  if (!exported) PAT_CUDA(launch_status_export(h->d_status, h->host_status_dev, s));
   PAT_CUDA(cudaStreamSynchronize(s));
   const int flag = *reinterpret_cast<volatile int*>(h->host_status);
   if (flag) {
