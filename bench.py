@@ -534,6 +534,17 @@ def main():
         bpb.sync()
         bpb.close()
 
+    if not args.no_forms:
+        # the off-line step on this frame: the table built by the host march
+        # (all host cores) and by the GPU solver (same first-order scheme)
+        from paper_1501_03869_gb300 import _lib
+        with BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+                flags=_lib.PAT_FLAG_GPU_TABLE) as bpg:
+            gpu_s = float(bpg.info["build_seconds"])
+        forms["table_build_c2"] = {"sensors": int(w.sensors.shape[0]),
+                                   "host_march_s": float(bp.info["build_seconds"]),
+                                   "host_threads": os.cpu_count(),
+                                   "gpu_solver_s": gpu_s}
     if not args.no_constant:
         forms["constant_speed_c2"] = constant_form(args, w, flush, stream)
     if not args.no_multi and world == 1:
