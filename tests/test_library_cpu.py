@@ -64,6 +64,27 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     assert e.value.status == _lib.PAT_ERR_INVALID
 
 
+def test_gpu_table_entries_reject_bad_arguments_before_touching_the_gpu():
+    """The GPU eikonal entries check their inputs on the host first: a source
+    outside the grid, a non-positive speed, or the second-order scheme (which
+    the GPU solver does not take) fail with PAT_ERR_INVALID, GPU or not."""
+    from paper_1501_03869_gb300 import PatError, fmm_gpu
+    sp = np.full((16, 16), 1500.0, dtype=np.float32)
+    origin = synth.centred_origin(sp.shape, 1e-4)
+    with pytest.raises(PatError) as e:
+        fmm_gpu(sp, 1e-4, origin, [[5e-3, 0.0, 0.0]])
+    assert e.value.status == _lib.PAT_ERR_INVALID
+    bad = sp.copy()
+    bad[3, 4] = 0.0
+    with pytest.raises(PatError) as e:
+        fmm_gpu(bad, 1e-4, origin, [[0.0, 0.0, 0.0]])
+    assert e.value.status == _lib.PAT_ERR_INVALID
+    with pytest.raises(PatError) as e:
+        table_host(sp, 1e-4, origin, synth.ring_sensors(4, 5e-4), 1e-8, 64, None,
+                   _lib.PAT_FLAG_GPU_TABLE | _lib.PAT_FLAG_FMM_SECOND_ORDER)
+    assert e.value.status == _lib.PAT_ERR_INVALID
+
+
 @pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("shape,seed", [((40, 33), 1), ((12, 11, 10), 2)])
 def test_host_fmm_matches_oracle(shape, seed, order):
