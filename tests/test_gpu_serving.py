@@ -128,3 +128,27 @@ def test_host_side_failures(subjects):
     st, _ = tiny.poll(t, 20_000_000)
     assert st == _lib.PAT_ERR_OOM
     tiny.close()
+
+
+def test_subject_with_gpu_table_and_solid_angle_handle(subjects):
+    """A subject registered with its table solved on the GPU (PAT_FLAG_GPU_TABLE)
+    serves the bits of a handle built the same way; the GPU-built table agrees
+    with the host-built one to rounding, so the images agree to ~1e-6."""
+    ws, refs = subjects
+    w = ws[0]
+    with BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+            flags=_lib.PAT_FLAG_GPU_TABLE) as bp:
+        ref = [bp.reconstruct(torch.from_numpy(w.signals[f:f + 1]).cuda()).cpu().numpy()[0]
+               for f in range(3)]
+        bp.sync()
+    srv = Server(hbm_budget=1 << 30, max_batch_frames=4)
+    sid = srv.register(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+                       flags=_lib.PAT_FLAG_GPU_TABLE)
+    outs = [np.empty(w.speed.shape, np.float32) for _ in range(3)]
+    ts = [srv.submit(sid, w.signals[f], outs[f]) for f in range(3)]
+    for f, t in enumerate(ts):
+        srv.wait(t)
+        assert np.array_equal(outs[f], ref[f])
+        host = refs[0][f]
+        assert np.linalg.norm(outs[f] - host) <= 1e-6 * np.linalg.norm(host)
+    srv.close()
