@@ -130,7 +130,7 @@ def test_host_side_failures(subjects):
     tiny.close()
 
 
-def test_subject_with_gpu_table_and_solid_angle_handle(subjects):
+def test_subject_with_gpu_table(subjects):
     """A subject registered with its table solved on the GPU (PAT_FLAG_GPU_TABLE)
     serves the bits of a handle built the same way; the GPU-built table agrees
     with the host-built one to rounding, so the images agree to ~1e-6."""
