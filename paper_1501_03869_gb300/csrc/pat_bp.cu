@@ -312,17 +312,36 @@ extern "C" pat_status pat_bp_set_solid_angle(pat_bp_t h, const double* normals_h
     return fail(PAT_ERR_INVALID, err);
   PAT_CUDA(cudaDeviceSynchronize());  // no launch of this handle may still read the old buffers
   const std::vector<float> ones(size_t(h->ns), 1.0f);
+  // Allocate everything first (device buffers and, with a host mirror, new
+  // pinned mirrors), so a failure leaves the handle exactly as it was.
   float* d_wa = nullptr;
   float4* d_px = nullptr;
-  if (cudaMalloc(&d_wa, wanchor.size() * 4) != cudaSuccess ||
-      (!h->delays && cudaMalloc(&d_px, pix.size() * 4) != cudaSuccess)) {
+  void* new_mirror[2] = {nullptr, nullptr};  // pixel terms, weight anchors
+  const std::vector<float>* src[2] = {&pix, &wanchor};
+  auto release = [&]() {
     cudaFree(d_wa);
+    cudaFree(d_px);
+    for (void* m : new_mirror) cudaFreeHost(m);
+  };
+  bool ok = cudaMalloc(&d_wa, wanchor.size() * 4) == cudaSuccess &&
+            (h->delays || cudaMalloc(&d_px, pix.size() * 4) == cudaSuccess);
+  if (ok && h->mirror[0])
+    for (int k = 0; k < 2 && ok; ++k) {
+      if (k == 0 && h->delays) continue;  // the constant-speed pixel terms are unchanged
+      ok = cudaMallocHost(&new_mirror[k], src[k]->size() * 4) == cudaSuccess;
+    }
+  if (!ok) {
+    release();
     return fail(PAT_ERR_OOM, "solid-angle weights");
   }
-  PAT_CUDA(cudaMemcpy(d_wa, wanchor.data(), wanchor.size() * 4, cudaMemcpyHostToDevice));
-  if (d_px) PAT_CUDA(cudaMemcpy(d_px, pix.data(), pix.size() * 4, cudaMemcpyHostToDevice));
+  cudaError_t e = cudaMemcpy(d_wa, wanchor.data(), wanchor.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && d_px) e = cudaMemcpy(d_px, pix.data(), pix.size() * 4, cudaMemcpyHostToDevice);
   // the solid angle replaces the per-sensor weights
-  PAT_CUDA(cudaMemcpy(h->d_w, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice));
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_w, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(e, "solid-angle weights upload");
+  }
   cudaFree(h->d_wanchor);
   h->d_wanchor = d_wa;
   if (d_px) {
@@ -332,20 +351,13 @@ extern "C" pat_status pat_bp_set_solid_angle(pat_bp_t h, const double* normals_h
   h->wgt = 1;
   if (h->mirror[0]) {  // keep the host mirror complete: weights, pixel terms, anchors
     std::memcpy(h->mirror[4], ones.data(), ones.size() * 4);
-    const std::vector<float>* src[2] = {&pix, &wanchor};
     for (int k = 0; k < 2; ++k) {
+      if (!new_mirror[k]) continue;
       const int i = 5 + k;
-      if (k == 0 && h->delays) continue;  // the constant-speed pixel terms are unchanged
-      const size_t bytes = src[k]->size() * 4;
-      if (h->mirror_bytes[i] != bytes) {
-        cudaFreeHost(h->mirror[i]);
-        h->mirror[i] = nullptr;
-        h->mirror_bytes[i] = 0;
-        if (cudaMallocHost(&h->mirror[i], bytes) != cudaSuccess)
-          return fail(PAT_ERR_OOM, "pinned host mirror");
-        h->mirror_bytes[i] = bytes;
-      }
-      std::memcpy(h->mirror[i], src[k]->data(), bytes);
+      std::memcpy(new_mirror[k], src[k]->data(), src[k]->size() * 4);
+      cudaFreeHost(h->mirror[i]);
+      h->mirror[i] = new_mirror[k];
+      h->mirror_bytes[i] = src[k]->size() * 4;
     }
   }
   return PAT_OK;
