@@ -61,6 +61,17 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(value, world, dist=None, device=None):
+    """The largest of the ranks' values, returned on every rank (the replicas'
+    timed region ends when the slowest one does); one rank: unchanged."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -459,10 +470,7 @@ def main():
     bp.sync()
     step_ms = [a.elapsed_time(b) for a, b in recs]
     tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(tot_ms, world, dist, dev)
     ms_per_step = tot_ms / args.steps
     value = world * updates * args.steps / (tot_ms / 1e3) / 1e9
     clocks = clk.summary()
