@@ -91,9 +91,11 @@ typedef struct {
   int sensor_warps;     /* warps that share a tile's sensors inside one CTA   */
   int64_t table_bytes;  /* device bytes of the delay data: the travel-time
                            table, or the anchors and pixel terms (constant c)  */
-  double build_seconds; /* host time of the table (or anchor) build           */
+  double build_seconds; /* wall time of the table (or anchor) build           */
   int delays;           /* 0 fast-marching table, 1 constant speed            */
   double c0;            /* the constant speed (m/s) when delays == 1, else 0  */
+  int solid_angle;      /* 1 after pat_bp_set_solid_angle (exact BP weights)  */
+  int gpu_table;        /* 1 if the table's times were solved on the GPU      */
 } pat_bp_info_t;
 
 const char* pat_status_str(pat_status s);

@@ -102,8 +102,11 @@ class BP:
                           ctypes.byref(h)), what)
         self._h = h
         self._lib = lib
+        self._refresh_info()
+
+    def _refresh_info(self):
         inf = _lib.PatInfo()
-        _lib.check(lib.pat_bp_info(h, ctypes.byref(inf)), "pat_bp_info")
+        _lib.check(self._lib.pat_bp_info(self._h, ctypes.byref(inf)), "pat_bp_info")
         self.info = {k: getattr(inf, k) for k, _ in _lib.PatInfo._fields_}
 
     def set_solid_angle(self, normals, elem, omega0):
@@ -119,6 +122,7 @@ class BP:
             raise ValueError("normals must be [ns, 3] and elem [ns]")
         _lib.check(self._lib.pat_bp_set_solid_angle(self._h, nrm.ctypes.data, el.ctypes.data,
                                                     float(omega0)), "pat_bp_set_solid_angle")
+        self._refresh_info()
         return self
 
     # ------------------------------------------------------------ lifecycle --

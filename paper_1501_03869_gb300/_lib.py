@@ -52,7 +52,7 @@ class PatInfo(ctypes.Structure):
                 ("n_tiles", ctypes.c_int), ("window", ctypes.c_int), ("split", ctypes.c_int),
                 ("sensor_warps", ctypes.c_int), ("table_bytes", ctypes.c_int64),
                 ("build_seconds", ctypes.c_double), ("delays", ctypes.c_int),
-                ("c0", ctypes.c_double)]
+                ("c0", ctypes.c_double), ("solid_angle", ctypes.c_int), ("gpu_table", ctypes.c_int)]
 
 
 class PatPlanInfo(ctypes.Structure):

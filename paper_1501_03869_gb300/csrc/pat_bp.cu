@@ -838,6 +838,8 @@ extern "C" pat_status pat_bp_info(pat_bp_t h, pat_bp_info_t* info) {
   info->build_seconds = h->build_seconds;
   info->delays = h->delays;
   info->c0 = h->c0;
+  info->solid_angle = h->wgt;
+  info->gpu_table = (h->flags & PAT_FLAG_GPU_TABLE) != 0 && !h->delays;
   return PAT_OK;
 }
 
@@ -946,6 +948,7 @@ extern "C" pat_status pat_table_host(const float* speed_host, const pat_grid* gr
   info->window = tab.W;
   info->table_bytes = int64_t(tab.u.size()) * 4;
   info->build_seconds = tab.build_seconds;
+  info->gpu_table = (flags & PAT_FLAG_GPU_TABLE) != 0;
   if (u_host) std::memcpy(u_host, tab.u.data(), tab.u.size() * 4);
   if (base_host) std::memcpy(base_host, tab.base.data(), tab.base.size() * 4);
   if (slot_host) {

@@ -33,6 +33,7 @@ def _gpu():
 def _both(speed, dx, origin, sensors, dt, nt, mask, flags=0):
     host = table_host(speed, dx, origin, sensors, dt, nt, mask, flags)
     gpu = table_host(speed, dx, origin, sensors, dt, nt, mask, flags | GPU)
+    assert host[0]["gpu_table"] == 0 and gpu[0]["gpu_table"] == 1
     return host, gpu
 
 

@@ -101,7 +101,9 @@ def test_ring_table_handle_matches_oracle():
     # inside the closed ring the weights of a pixel sum to 1 (the oracle's pin)
     assert np.abs(W.sum(axis=0) - 1.0).max() < 1e-6
     with BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, w.mask) as bp:
+        assert bp.info["solid_angle"] == 0
         bp.set_solid_angle(nrm, elem, 2.0 * math.pi)
+        assert bp.info["solid_angle"] == 1
         img = run(bp, w.signals)
     check_fp32(img, ref)
     assert np.all(img[:, w.mask == 0] == 0.0)
