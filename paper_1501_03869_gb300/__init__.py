@@ -3,10 +3,12 @@
 Wang & Jing, "A fast marching method based back projection algorithm for
 photoacoustic tomography in heterogeneous media":
   * Sec. II-B: fast-marching travel times from each sensor (off line, once per
-    speed map) -- built on the host inside :class:`BP` creation;
+    speed map) -- built inside :class:`BP` creation by the host march or, with
+    PAT_FLAG_GPU_TABLE, by the GPU solver (:func:`fmm_gpu` solves whole grids);
   * Sec. II-C, Eq. (BP): per-frame back projection of 2p - 2t dp/dt at those
     travel times -- CUDA kernels for sm_103a behind the C ABI of
-    ``include/pat_bp.h``.
+    ``include/pat_bp.h``; :meth:`BP.constant` for the constant-speed
+    comparison, :meth:`BP.set_solid_angle` for the exact back projection.
 
 PyTorch is used for device memory and streams only.  The CUDA library is
 loaded lazily; any call fails loudly when it has not been built.
@@ -55,6 +57,8 @@ class BP:
     dt, n_samples   sampling of every signal (t_k = k dt)
     mask       grid-shaped, nonzero = reconstruct (None = all nodes)
     weights    [ns] w_s of Eq. (BP) (None = 1/ns)
+    flags      PAT_FLAG_* (tile size, compact output, host mirror, second-order
+               or GPU-solved table, ...)
     """
 
     def __init__(self, speed, dx, origin, sensors, dt, n_samples, mask=None, weights=None,
@@ -473,7 +477,9 @@ def fmm_gpu(speed, dx, origin, sources):
 
 
 def table_host(speed, dx, origin, sensors, dt, n_samples, mask=None, flags=0):
-    """The device table, built on the host only: (info, u, base, slot)."""
+    """The table pat_bp_create would upload, returned to the host: (info, u,
+    base, slot).  Built by the host march, or by the GPU solver with
+    flags |= PAT_FLAG_GPU_TABLE."""
     lib = _lib.load()
     speed = np.ascontiguousarray(speed, dtype=np.float32)
     g = _lib.make_grid(speed.shape, dx, origin)
