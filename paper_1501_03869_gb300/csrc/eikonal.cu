@@ -479,7 +479,6 @@ bool gpu_eikonal_slot_times(GpuEikonal* e, const double* sensors, int nb, double
     p.n[d] = g.n[d];
     p.bn[d] = e->bn[d];
   }
-  p.ndim = g.ndim;
   p.total = e->total;
   p.n_blocks = e->n_blocks;
   p.stop_after = stop_after;
