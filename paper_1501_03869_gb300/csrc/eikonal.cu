@@ -64,7 +64,6 @@ struct EikParams {
   double tau;           // this round's acceptance bound (s)
   int n[3];             // nodes per axis (x first)
   int bn[3];            // blocks per axis
-  int ndim;
   int64_t total;
   int n_blocks;
   double stop_after;
