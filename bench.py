@@ -180,6 +180,39 @@ def oracle_cpu_rate(w, n_sensors, seconds, frames=1):
     return n * n_sensors * pix.size / el, el, n
 
 
+def _oracle_chunk(args):
+    """One worker of the all-cores oracle timing: the oracle's back projection
+    over a chunk of the pixels, repeated for about `seconds`."""
+    T, p, dt, seconds = args
+    import oracle
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.bp(T, p, dt)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return n * T.shape[0] * T.shape[1], time.perf_counter() - t0
+
+
+def oracle_cpu_rate_all_cores(w, n_sensors, seconds):
+    """The same oracle back projection, unmodified, run over pixel chunks by one
+    process per host core (a spawn-started pool: this runs after CUDA work).
+    Returns (updates/s summed over the workers' rates, workers)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import oracle
+    pix = np.flatnonzero(w.mask.ravel())
+    T = oracle.travel_table(w.speed, w.dx, w.origin, w.sensors[:n_sensors], pix)
+    p = w.signals[0, :n_sensors].astype(np.float64)
+    n_w = max(1, os.cpu_count() or 1)
+    chunks = np.array_split(np.arange(pix.size), n_w)
+    jobs = [(np.ascontiguousarray(T[:, c]), p, w.dt, seconds) for c in chunks if c.size]
+    with cf.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_chunk, jobs))
+    return sum(u / t for u, t in res), len(jobs)
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -568,6 +601,11 @@ def main():
         cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} runs of the FP64 oracle back projection over the first {n_s} "
                          f"sensors x {n_pix} pixels ({el:.1f} s, table built before timing)"}
+        if not args.no_forms:
+            rate_all, n_w = oracle_cpu_rate_all_cores(w, n_s, min(args.cpu_seconds, 5.0))
+            forms["cpu_oracle_all_cores"] = {
+                "value": rate_all / 1e9, "unit": UNIT, "cores": n_w, "kind": "oracle",
+                "sample": f"the same back projection over pixel chunks, one process per host core"}
 
     if rank == 0:
         line = {
