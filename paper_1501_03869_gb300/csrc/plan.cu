@@ -144,20 +144,34 @@ void drop_graph(pat_plan_t pl) {
 
 namespace {
 
-// Point every descriptor at the handles' current buffers (a handle's own
-// calls may have grown them since the plan was shaped).
+// Point every descriptor at the handles' current buffers: a handle's own
+// calls may have grown its working buffers since the plan was shaped, and an
+// eviction and restore reallocates its table, so every handle-owned pointer
+// is taken again.  A handle whose kernel mode changed since (solid-angle
+// weights set) no longer fits the plan's launch shape.
 pat_status refresh_buffers(pat_plan_t pl) {
   for (size_t i = 0; i < pl->hs.size(); ++i) {
     pat_bp_t h = pl->hs[i];
     if (h->evicted) return fail(PAT_ERR_INVALID, "a plan handle's table is evicted");
+    if (h->wgt != pl->cfg.wgt || h->delays != pl->cfg.delays)
+      return fail(PAT_ERR_INVALID, "a plan handle changed its weights since the plan was made");
     pat_status st = ensure_buffers_fb(h, pl->frames[i], pl->FB);
     if (st != PAT_OK) return st;
+    pl->pre->inst[i].weights = h->d_w;
     pl->pre->inst[i].b = h->d_b;
     pl->pre->inst[i].m = h->d_m;
-    pl->gat->inst[i].b = h->d_b;
-    pl->gat->inst[i].m = h->d_m;
-    pl->gat->inst[i].part = h->d_part;
-    pl->gat->inst[i].counter = h->d_counter;
+    InstDesc& d = pl->gat->inst[i];
+    d.u = h->d_u;
+    d.anchor = h->d_anchor;
+    d.pix = h->d_pix;
+    d.wanchor = h->wgt ? h->d_wanchor : nullptr;
+    d.base = h->d_base;
+    d.slot = h->d_slot;
+    d.zero_runs = h->d_zero_runs;
+    d.b = h->d_b;
+    d.m = h->d_m;
+    d.part = h->d_part;
+    d.counter = h->d_counter;
   }
   return PAT_OK;
 }

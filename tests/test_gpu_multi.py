@@ -109,3 +109,39 @@ def test_cheapest_instances_match_oracle(c4):
             e = np.linalg.norm(single[i][f] - ref[f]) / np.linalg.norm(ref[f])
             assert e <= FP32_REL_L2, (i, f, e)
             assert np.abs(single[i][f] - ref[f]).max() <= FP32_MAX_ABS_FRAC * p0
+
+
+def test_plan_follows_evict_restore_and_refuses_changed_weights():
+    """A plan's descriptors follow its handles' buffers: after an eviction and
+    a restore (which reallocate the table) the plan, graph-replayed, still
+    gives the single-handle bits; a handle switched to solid-angle weights
+    after the plan was made is refused instead of being read in the old mode."""
+    import math
+    from paper_1501_03869_gb300 import PatError, _lib
+    a = synth.config1(n_frames=2)
+    b = synth.config1(n_frames=3, inst=1, cfg_id=7)
+    ha = BP(a.speed, a.dx, a.origin, a.sensors, a.dt, a.nt, a.mask, flags=_lib.PAT_FLAG_HOST_MIRROR)
+    hb = BP(b.speed, b.dx, b.origin, b.sensors, b.dt, b.nt, b.mask)
+    sa, sb = torch.from_numpy(a.signals).cuda(), torch.from_numpy(b.signals).cuda()
+    ref_a, ref_b = ha.reconstruct(sa).cpu().numpy(), hb.reconstruct(sb).cpu().numpy()
+    plan = Plan([ha, hb], [2, 3], graph=True)
+    for rep in range(3):
+        if rep == 1:
+            ha.evict()
+            junk = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")  # move the allocator on
+            ha.restore()
+            del junk
+        outs = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.out_shapes()]
+        plan.execute([sa, sb], outs)
+        plan.sync()
+        assert np.array_equal(outs[0].cpu().numpy(), ref_a)
+        assert np.array_equal(outs[1].cpu().numpy(), ref_b)
+    nrm = -a.sensors / np.linalg.norm(a.sensors, axis=1, keepdims=True)
+    elem = np.full(a.sensors.shape[0], 2 * math.pi * np.linalg.norm(a.sensors[0]) / a.sensors.shape[0])
+    ha.set_solid_angle(nrm, elem, 2 * math.pi)
+    outs = [torch.empty(s, dtype=torch.float32, device="cuda") for s in plan.out_shapes()]
+    with pytest.raises(PatError):
+        plan.execute([sa, sb], outs)
+    plan.close()
+    ha.close()
+    hb.close()
