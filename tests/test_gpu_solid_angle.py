@@ -238,3 +238,30 @@ def test_bad_arguments_rejected():
             bp.set_solid_angle(nrm, -elem, 2.0 * math.pi)
         with pytest.raises(PatError):
             bp.set_solid_angle(nrm, elem, 0.0)
+
+
+def test_hemisphere_table_handle_3d():
+    """Weights on a 3-D stored-table handle (pixel terms in node units): the
+    scaled serving subject's speed map with 48 sensors on a hemisphere of
+    radius 13 voxels inside the grid, the voxels within 10 of its centre,
+    against the oracle's fast marching."""
+    w = synth.config5_subject(1, n_frames=1, n_sensors=8, shape=(20, 32, 32), nt=512)
+    centre = np.array([15.5, 15.5, 2.0]) * w.dx
+    R = 13.0 * w.dx
+    sens = synth.fibonacci_hemisphere(48, R, centre)
+    nrm = (centre[None, :] - sens) / R
+    elem = np.full(48, 2.0 * math.pi * R * R / 48)
+    rng = synth.rng_for(43, 0, 0, 2)
+    c = centre[None, :] + np.array([[2.0, -1.0, 3.0], [-3.0, 2.0, 5.0]]) * w.dx
+    sig = synth.render_signals(w.speed, w.dx, w.origin, sens, c, np.full(2, 1.5 * w.dx),
+                               np.array([1.0, 0.6]), w.dt, w.nt, 0.01, rng)[None]
+    # voxels within 10 of the centre, 3 or more voxels from every element
+    mask = (synth.node_radius_px(w.speed.shape, (15.5, 15.5, 2.0)) < 10.0).astype(np.uint8)
+    pix = np.flatnonzero(mask.ravel())
+    T = travel_table("c5_small_hemi48", w.speed, w.dx, w.origin, sens, pix)
+    ref, _ = oracle_images(w.speed.shape, w.dx, w.origin, mask, sens, nrm, elem, 2.0 * math.pi, T,
+                           sig, w.dt)
+    with BP(w.speed, w.dx, w.origin, sens, w.dt, w.nt, mask) as bp:
+        bp.set_solid_angle(nrm, elem, 2.0 * math.pi)
+        img = run(bp, sig)
+    check_fp32(img, ref)
