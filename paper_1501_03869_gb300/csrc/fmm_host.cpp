@@ -63,38 +63,39 @@ int64_t FastMarcher::to_padded(int64_t v) const {
   return p;
 }
 
-bool FastMarcher::key_less(int64_t a, int64_t b) const {
-  double ta = t_[a], tb = t_[b];
-  return ta < tb || (ta == tb && a < b);
-}
-
+// The pop order depends only on the total order of (T, node), not on the
+// heap's shape, so the accepted sequence (and every value) is that of any
+// exact priority queue with this order.
 void FastMarcher::heap_up(int64_t i) {
-  int64_t node = heap_[i];
+  const HeapEntry e = heap_[i];
   while (i > 0) {
-    int64_t up = (i - 1) >> 1;
-    if (!key_less(node, heap_[up])) break;
+    const int64_t up = (i - 1) >> 2;
+    if (!key_less(e, heap_[up])) break;
     heap_[i] = heap_[up];
-    pos_[heap_[i]] = int32_t(i);
+    pos_[heap_[i].node] = int32_t(i);
     i = up;
   }
-  heap_[i] = node;
-  pos_[node] = int32_t(i);
+  heap_[i] = e;
+  pos_[e.node] = int32_t(i);
 }
 
 void FastMarcher::heap_down(int64_t i) {
   const int64_t n = int64_t(heap_.size());
-  int64_t node = heap_[i];
+  const HeapEntry e = heap_[i];
   for (;;) {
-    int64_t c = 2 * i + 1;
-    if (c >= n) break;
-    if (c + 1 < n && key_less(heap_[c + 1], heap_[c])) ++c;
-    if (!key_less(heap_[c], node)) break;
+    const int64_t c0 = 4 * i + 1;
+    if (c0 >= n) break;
+    int64_t c = c0;
+    const int64_t c_end = std::min(c0 + 4, n);
+    for (int64_t k = c0 + 1; k < c_end; ++k)
+      if (key_less(heap_[k], heap_[c])) c = k;
+    if (!key_less(heap_[c], e)) break;
     heap_[i] = heap_[c];
-    pos_[heap_[i]] = int32_t(i);
+    pos_[heap_[i].node] = int32_t(i);
     i = c;
   }
-  heap_[i] = node;
-  pos_[node] = int32_t(i);
+  heap_[i] = e;
+  pos_[e.node] = int32_t(i);
 }
 
 double FastMarcher::local_solve(int64_t pv, double hf) const {
@@ -245,9 +246,10 @@ bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_a
           t_[q] = cand;
           if (s == kFar) {
             st_[q] = kTrial;
-            heap_.push_back(q);
+            heap_.push_back(HeapEntry{cand, q});
             heap_up(int64_t(heap_.size()) - 1);
           } else {
+            heap_[pos_[q]].t = cand;  // a decrease: the entry moves up only
             heap_up(pos_[q]);
           }
         }
@@ -258,14 +260,14 @@ bool FastMarcher::solve(const double* src, std::vector<double>& T, double stop_a
 
   while (!heap_.empty()) {
     if (n_targets > 0 && wanted_left <= 0) break;
-    int64_t pv = heap_[0];
-    if (t_[pv] > stop_after) break;
-    int64_t last = heap_.back();
+    const int64_t pv = heap_[0].node;
+    if (heap_[0].t > stop_after) break;
+    const HeapEntry last = heap_.back();
     heap_.pop_back();
     pos_[pv] = -1;
     if (!heap_.empty()) {
       heap_[0] = last;
-      pos_[last] = 0;
+      pos_[last.node] = 0;
       heap_down(0);
     }
     st_[pv] = kAccepted;

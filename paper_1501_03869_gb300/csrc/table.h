@@ -75,15 +75,23 @@ class FastMarcher {
   int64_t ptotal_;
   std::vector<double> t_;     // padded arrival times
   std::vector<uint8_t> st_;   // padded states
-  std::vector<int32_t> pos_;  // heap position of each padded node, -1 if absent
-  std::vector<int64_t> heap_; // padded node ids
+  // Trial nodes in a 4-ary min-heap of (T, node) entries ordered by T, then
+  // node id; the key lives in the entry, so sifting does not chase t_.
+  struct HeapEntry {
+    double t;
+    int64_t node;
+  };
+  std::vector<int32_t> pos_;     // heap position of each padded node, -1 if absent
+  std::vector<HeapEntry> heap_;
   std::vector<double> hf_;    // padded dx / c
   std::vector<double> c_;     // padded c
   std::vector<uint8_t> wanted_;
   int64_t to_padded(int64_t v) const;
   void heap_up(int64_t i);
   void heap_down(int64_t i);
-  bool key_less(int64_t a, int64_t b) const;
+  static bool key_less(const HeapEntry& a, const HeapEntry& b) {
+    return a.t < b.t || (a.t == b.t && a.node < b.node);
+  }
   double local_solve(int64_t pv, double hf) const;
   double local_solve2(int64_t pv, double hf) const;
 };
