@@ -321,7 +321,10 @@ pat_status pat_plan_create(const pat_bp_t* handles, const int* n_frames, int n, 
  * in pat_bp_reconstruct.  Asynchronous on stream, except that the first call
  * of an autotuning plan synchronises while it times candidate shapes (that
  * call must not be captured by the caller).  Executions of one plan, and of
- * plans or calls sharing a handle, must not overlap on the GPU. */
+ * plans or calls sharing a handle, must not overlap on the GPU.  On the host,
+ * an execution holds every handle of the plan (the same lock as the handle's
+ * own calls) while it enqueues its work, so handle calls from other threads
+ * wait for it instead of changing buffers the launch reads. */
 pat_status pat_plan_execute(pat_plan_t plan, const void* const* signals_dev,
                             const float* const* scales_dev, float* const* outs_dev,
                             pat_stream_t stream);

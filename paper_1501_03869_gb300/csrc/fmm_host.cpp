@@ -8,8 +8,10 @@
 // off-line step, done once per speed map and sensor layout.
 //
 // Implementation choices of this file: a one-node ghost layer around the grid
-// (no bounds tests in the neighbour loop), an indexed binary heap with
-// decrease-key, the root of the m-axis quadratic written as
+// (no bounds tests in the neighbour loop), an indexed 4-ary heap of (T, node)
+// entries with the key held inline and decrease-key (ordered by (T, node), so
+// the pop order is that of any exact priority queue), the root of the m-axis
+// quadratic written as
 // (S + sqrt(S^2 - m (Q - (h/c)^2))) / m, early exit once every wanted pixel is
 // accepted or the front passes the end of the record, and one std::thread per
 // core, each marching whole sensors.

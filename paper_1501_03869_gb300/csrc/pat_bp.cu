@@ -524,20 +524,25 @@ InstDesc make_desc(pat_bp_t h, float* out, int n_frames, int FB, int wst) {
 }
 
 int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm) {
+  // keyed by the current device too: devices of one process may differ in
+  // multiprocessor count and shared memory
   struct Key {
-    int P, FB, SW, S, stages, fmt, wst, delays, wgt;
+    int dev, n_sm, P, FB, SW, S, stages, fmt, wst, delays, wgt, direct;
   };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   static std::mutex mu;
   static std::vector<std::pair<Key, int>> cache;
   std::lock_guard<std::mutex> lk(mu);
   for (auto& e : cache) {
     const Key& k = e.first;
-    if (k.P == c.P && k.FB == c.FB && k.SW == c.SW && k.S == c.S && k.stages == c.stages &&
-        k.fmt == fmt && k.wst == wst && k.delays == c.delays && k.wgt == c.wgt)
+    if (k.dev == dev && k.n_sm == n_sm && k.P == c.P && k.FB == c.FB && k.SW == c.SW &&
+        k.S == c.S && k.stages == c.stages && k.fmt == fmt && k.wst == wst &&
+        k.delays == c.delays && k.wgt == c.wgt && k.direct == c.direct)
       return e.second;
   }
   const int r = gather_resident_ctas(c, fmt, wst, n_sm);
-  cache.push_back({Key{c.P, c.FB, c.SW, c.S, c.stages, fmt, wst, c.delays, c.wgt}, r});
+  cache.push_back({Key{dev, n_sm, c.P, c.FB, c.SW, c.S, c.stages, fmt, wst, c.delays, c.wgt, c.direct}, r});
   return r;
 }
 

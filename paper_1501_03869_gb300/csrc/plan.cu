@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -420,6 +421,20 @@ static pat_status plan_new(const pat_bp_t* handles, const int* n_frames, int n, 
   return PAT_OK;
 }
 
+// Locks every handle of a plan for one execution, in address order (so two
+// plans that share handles cannot deadlock): an execution may grow a handle's
+// working buffers and reads its table pointers, which the handle's own calls
+// (reconstruct, evict, restore, set_solid_angle) change under the same lock.
+struct HandleLocks {
+  std::vector<std::unique_lock<std::mutex>> locks;
+  explicit HandleLocks(const std::vector<pat_bp_t>& hs) {
+    std::vector<pat_bp_t> order(hs);
+    std::sort(order.begin(), order.end(), std::less<pat_bp_t>());
+    locks.reserve(order.size());
+    for (pat_bp_t h : order) locks.emplace_back(h->mu);
+  }
+};
+
 static pat_status plan_run(pat_plan_t pl, const void* const* sig, const float* const* scales,
                            float* const* outs, cudaStream_t stream) {
   if (!sig || !outs) return fail(PAT_ERR_INVALID, "signals/outs NULL");
@@ -429,6 +444,7 @@ static pat_status plan_run(pat_plan_t pl, const void* const* sig, const float* c
       return fail(PAT_ERR_INVALID, "16-bit signals need scales");
   }
   PAT_CUDA(cudaSetDevice(pl->device));
+  const HandleLocks locks(pl->hs);
   pat_status st;
   if ((pl->flags & PAT_PLAN_AUTOTUNE) && !pl->tuned) {
     if ((st = autotune(pl, sig, scales, outs, stream, false)) != PAT_OK) return st;
