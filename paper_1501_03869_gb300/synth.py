@@ -365,18 +365,19 @@ def config1(n_frames=1, inst=0, cfg_id=1, noise=0.01, arrivals=None):
     return Workload("c1", speed, dx, origin, sensors, mask, dt, nt, np.stack(sig), np.stack(p0))
 
 
-def config2(n_frames=1, inst=0, noise=0.01, n_lines=20, arrivals=None):
+def config2(n_frames=1, inst=0, noise=0.01, n_lines=20, arrivals=None, n_sensors=512,
+            nt=2048, dt=12.5e-9):
     """Paper-shaped frame: 256x256, dx 0.1 mm, skull ring (inner radius 86 +- 2 px,
     thickness 25 +- 5 px, speed field 2200-3000 m/s), 512 sensors at r = 120 px,
     2048 samples at 12.5 ns, the 21 323 nodes nearest the centre, 20 line
-    absorbers of 10-60 px rendered as 1-px discs every 0.5 px."""
+    absorbers of 10-60 px rendered as 1-px discs every 0.5 px.  Tests may ask
+    for more sensors on the same ring and a finer sampling of the record."""
     shape, dx = (256, 256), 0.1e-3
     origin = centred_origin(shape, dx)
     speed = skull_ring_2d(shape, 86.0, 25.0, rng_for(2, inst, 0, 1), r_in_var=2.0,
                           thick_var=5.0, skull_speed=None)
-    sensors = ring_sensors(512, 120.0 * dx)
+    sensors = ring_sensors(n_sensors, 120.0 * dx)
     mask = nearest_nodes_mask(shape, 21323)
-    dt, nt = 12.5e-9, 2048
     sig, p0 = [], []
     for f in range(n_frames):
         rng = rng_for(2, inst, f, 2)
