@@ -62,17 +62,101 @@ constexpr float kFarOffset = 1.0e30f;
 // N = (n, d); w = scale (n . v) / |v|^d, d = 2 or 3 (the same for every sensor
 // of a handle: a uniform branch).  Both gathers use this function, so a frame
 // gets the same weights alone and in a batch.
+__device__ __forceinline__ float solid_angle_weight(const float4 pq, float4 E, float4 N) {
+  const float v0 = fmaf(0.5f, pq.x, E.x), v1 = fmaf(0.5f, pq.y, E.y), v2 = fmaf(0.5f, pq.z, E.z);
+  const float r2 = fmaxf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)), 1.0e-30f);
+  const float nv = fmaf(N.x, v0, fmaf(N.y, v1, N.z * v2));
+  const float y = rsqrtf(r2);
+  const float inv = N.w == 3.0f ? y * y * y : y * y;
+  return E.w * (nv * inv);
+}
+
 __device__ __forceinline__ void solid_angle_weights(float (&ww)[4], const float4 (&pq)[4], float4 E,
                                                     float4 N) {
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const float v0 = fmaf(0.5f, pq[x].x, E.x), v1 = fmaf(0.5f, pq[x].y, E.y),
-                v2 = fmaf(0.5f, pq[x].z, E.z);
-    const float r2 = fmaxf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)), 1.0e-30f);
-    const float nv = fmaf(N.x, v0, fmaf(N.y, v1, N.z * v2));
-    const float y = rsqrtf(r2);
-    const float inv = N.w == 3.0f ? y * y * y : y * y;
-    ww[x] = E.w * (nv * inv);
+  for (int x = 0; x < 4; ++x) ww[x] = solid_angle_weight(pq[x], E, N);
+}
+
+// Constant-speed delay (window offset) of one pixel for a sensor's anchor
+// (A, B) -- the arithmetic of gather_sensor_const below, for one pixel.
+__device__ __forceinline__ float const_delay(const float4 pq, float4 A, float4 B) {
+  if (B.w == 0.0f) {
+    const float num = fmaf(pq.x, A.x, fmaf(pq.y, A.y, fmaf(pq.z, A.z, pq.w)));
+    const float s = num + B.z;
+    const float y = rsqrtf(s);
+    const float da = s * y - A.w;
+    const float r = fmaf(-da, da, fmaf(-2.0f * A.w, da, num));
+    const float v = fmaf(r, 0.5f * y, da) + B.x;
+    return v > B.y ? kFarOffset : fmaxf(v, 0.0f);
+  }
+  const float d0 = fmaf(0.5f, pq.x, A.x), d1 = fmaf(0.5f, pq.y, A.y), d2 = fmaf(0.5f, pq.z, A.z);
+  const float s = fmaxf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), 1.0e-30f);
+  const float v = (s * rsqrtf(s) - A.w) + B.x;
+  return v > B.y ? kFarOffset : fmaxf(v, 0.0f);
+}
+
+// Units of 16 frames ("wide" units).  A row of the integrand holds 16 frames
+// (64 bytes: four 16-byte chunks of 4 frames); lane (g, c) = (lane / 4,
+// lane % 4) of a consumer warp owns frames 4c .. 4c + 3 of the warp's pixels
+// g, g + 8, ..., g + 56.  So the 8 lanes of a 16-byte shared-memory load phase
+// read whole rows of 2 pixels, and the chunks of row r are stored rotated,
+// physical chunk = c ^ ((r / 2) mod 4), which puts two rows that share their
+// bank half (r = r' mod 2) on different banks unless r = r' mod 8.  Window
+// copies start at rows that are multiples of 8 in global and shared memory,
+// so the rotation of a row is the same in both.
+__device__ __forceinline__ unsigned wide_chunk(unsigned r, int c) { return unsigned(c) ^ ((r >> 1) & 3u); }
+
+// One sensor of a stage for a wide unit: offsets uu of the lane's 8 pixels
+// (sample rows from the sensor's window start), multipliers of the lane's 4
+// frames; acc[j][f] += m_f * w_j * lerp.  Same arithmetic per (pixel, frame)
+// as lerp_accumulate.
+template <int FMT, int WGT>
+__device__ __forceinline__ void lerp_accumulate_wide(float (&acc)[8][4], const float (&uu)[8],
+                                                     const float (&ww)[8], const uint32_t* sm, int off,
+                                                     const uint32_t* sw, int Wst, int c) {
+  const unsigned lim = unsigned(Wst - off);
+  float mm[4];
+  {
+    const uint4 q = *reinterpret_cast<const uint4*>(sm + 4 * c);
+    mm[0] = __uint_as_float(q.x);
+    mm[1] = __uint_as_float(q.y);
+    mm[2] = __uint_as_float(q.z);
+    mm[3] = __uint_as_float(q.w);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const unsigned i = min(unsigned(__float2int_rz(uu[j])), lim);
+    const float ph = uu[j] - float(i);
+    const unsigned r = i + unsigned(off);
+    const uint4 q0 = *reinterpret_cast<const uint4*>(sw + r * 16u + (wide_chunk(r, c) << 2));
+    const uint32_t w0[4] = {q0.x, q0.y, q0.z, q0.w};
+    if constexpr (FMT == kBF32) {
+      const unsigned r1 = r + 1u;
+      const uint4 q1 = *reinterpret_cast<const uint4*>(sw + r1 * 16u + (wide_chunk(r1, c) << 2));
+      const uint32_t w1[4] = {q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const float b0 = __uint_as_float(w0[f]), b1 = __uint_as_float(w1[f]);
+        float v = fmaf(ph, b1 - b0, b0);
+        if constexpr (WGT != 0) v = __fmul_rn(ww[j], v);
+        acc[j][f] = fmaf(mm[f], v, acc[j][f]);
+      }
+    } else if constexpr (FMT == kBBF16P) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        float v = fmaf(ph, __uint_as_float(w0[f] & 0xffff0000u), __uint_as_float(w0[f] << 16));
+        if constexpr (WGT != 0) v = __fmul_rn(ww[j], v);
+        acc[j][f] = fmaf(mm[f], v, acc[j][f]);
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&w0[f]));
+        float v = fmaf(ph, h.y, h.x);
+        if constexpr (WGT != 0) v = __fmul_rn(ww[j], v);
+        acc[j][f] = fmaf(mm[f], v, acc[j][f]);
+      }
+    }
   }
 }
 
@@ -195,11 +279,16 @@ __device__ __forceinline__ void gather_sensor_const(float (&acc)[FB][4], const f
 }
 
 // Shared-memory layout of one pipeline stage (byte offsets); `mode` is the
-// kernel's: bit 0 constant-speed delays, bit 1 solid-angle weights.
+// kernel's: bit 0 constant-speed delays, bit 1 solid-angle weights.  A stage
+// holds up to S consecutive sensors of a segment -- as many as the row budget
+// Wst of the windows allows (the producer decides and writes (se, m_shift) to
+// the stage's header).
 //   u    [S][P] float            the tile's table rows of the stage's sensors,
 //                                or [S][8] float anchors (constant speed)
 //   wa   [S][8] float            solid-angle weight anchors (bit 1 only)
-//   m    [S4][FB] float          multipliers w_s * sigma
+//   m    [S4 + 4][FB] float      multipliers w_s * sigma, copied from the
+//                                16-byte-aligned sensor at or below the first
+//                                (the first sensor's sit m_shift entries in)
 //   off  [S4] int                window offset (rows) of each sensor
 //   win  [Wst + 4][FB] words     the stage's windows packed at `off`, then 4
 //                                zero rows that out-of-record pixels read
@@ -210,7 +299,7 @@ struct StageLayout {
     u = 0;
     wa = u + ((mode & 1) ? size_t(S) * 32 : size_t(S) * P * 4);
     m = wa + ((mode & 2) ? size_t(S) * 32 : 0);
-    off = m + size_t(S4) * FB * 4;
+    off = m + size_t(S4 + 4) * FB * 4;
     win = off + size_t(S4) * 4;
     bytes = win + size_t(Wst + 4) * FB * 4;
   }
@@ -251,11 +340,18 @@ constexpr int kRing = 16;  // unit indices in flight between the producer and th
 // anchor per sensor copied into each stage and the pixel terms.  The computed
 // delays hold more live registers; the minimum of resident CTAs keeps the
 // compiler from spilling them (0 leaves the table variants unconstrained).
+// Pixel groups across a tile: 128 pixels per consumer warp (4 per lane), or
+// 64 (8 per lane, 4 frames each) for wide 16-frame units.
+template <int P, int FB>
+constexpr int consumer_pixel_warps() { return FB == 16 ? P / 64 : P / 128; }
+
 template <int P, int FB, int FMT, int SW, int MODE>
-__global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB == 1 ? 3 : 2) : 0)
+__global__ void __launch_bounds__(32 * (consumer_pixel_warps<P, FB>() * SW + 3),
+                                  (MODE & 1) ? (FB == 1 ? 3 : (FB == 16 ? 1 : 2)) : 0)
     gather_kernel(const __grid_constant__ StreamParams p) {
   constexpr int DELAYS = MODE & 1, WGT = (MODE >> 1) & 1;
-  constexpr int PW = P / 128;   // warps across the tile's pixels
+  constexpr int PW = consumer_pixel_warps<P, FB>();  // warps across the tile's pixels
+  static_assert((SW & (SW - 1)) == 0, "sensor phases: a power of two");
   constexpr int NWC = PW * SW;  // consumer warps
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -264,6 +360,7 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
   int64_t* unit_ring = reinterpret_cast<int64_t*>(meta_bar + 2);  // [kRing]
   int64_t* red_unit = unit_ring + kRing;                           // [2]
   volatile int* abort_flag = reinterpret_cast<volatile int*>(red_unit + 2);
+  int2* stage_hdr = reinterpret_cast<int2*>(smem + 320);  // [kMaxStages] (sensors, m shift)
   int* meta = reinterpret_cast<int*>(smem + kHeaderBytes);  // [2][kMaxG] packed bases
   const StageLayout L(p.S, P, FB, p.Wst, MODE);
   unsigned char* stage0 = smem + kHeaderBytes + kMetaBytes;
@@ -320,17 +417,19 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
       abort_now();
       return false;
     };
-    // Issue stage st for sensors [s0, s0 + S) of unit q: the table block (part
-    // & 1) and/or the multipliers and windows (part & 2), which come from the
-    // preprocessing grid.  The stage's expected bytes are posted with the
-    // table block (or with everything when part == 3).
+    // Issue stage st of unit q from sensor s0: the sensors it takes are the
+    // longest run of at most S (and at most the segment's rest) whose windows
+    // fit the row budget Wst (at least one: Wst is at least the longest single
+    // window).  Part 1 posts the expected bytes and copies the table block
+    // (delay data), part 2 the multipliers and windows, which come from the
+    // preprocessing grid (part 3: both).  Returns the sensors taken; both
+    // parts compute the same.
     auto issue_chunk = [&](const UnitPos& q, const InstDesc& d, const int* mrow, int s0, int st,
-                           int part) {
-      const int se = min(p.S, q.s_hi - s0);
-      const int se4 = (se + 3) & ~3;
+                           int part) -> int {
+      const int avail = min(p.S, q.s_hi - s0);
       unsigned char* sb = stage0 + st * L.bytes;
       int bs = 0, wl = 0;
-      if (lane < se) {
+      if (lane < avail) {
         const uint32_t word = uint32_t(mrow[s0 - q.s_lo + lane]);
         bs = int(word & 0xffffu);
         wl = int(word >> 16);
@@ -341,21 +440,28 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
       }
-      const int total_w = __shfl_sync(0xffffffffu, incl, 31);
-      int off = incl - wl;
-      uint32_t wrows = uint32_t(total_w);
-      if (total_w > p.Wst) {  // cannot happen with a host-computed Wst; stay in bounds
-        if (lane == 0 && (part & 1)) atomicOr(p.status, kStatusBadConfig);
-        wl = 0;
-        off = 0;
-        wrows = 0;
+      const unsigned fit = __ballot_sync(0xffffffffu, lane < avail && incl <= p.Wst);
+      int se = __popc(fit);  // the windows' prefix sums grow: the fitting lanes are a prefix
+      bool bad = false;
+      if (se == 0) {  // cannot happen with a host-computed Wst; stay in bounds
+        bad = true;
+        se = 1;
       }
+      if (lane >= se || bad) wl = 0;
+      const int total_w = bad ? 0 : __shfl_sync(0xffffffffu, incl, se - 1);
+      const int off = bad ? 0 : incl - wl;
+      const int ma = s0 & ~3;                               // aligned first multiplier
+      const int mcount = ((s0 + se + 3) & ~3) - ma;         // <= S4 + 4
       if (part & 1) {
         if (lane < S4) reinterpret_cast<int*>(sb + L.off)[lane] = lane < se ? off : 0;
+        if (lane == 0) {
+          stage_hdr[st] = make_int2(se, s0 - ma);
+          if (bad) atomicOr(p.status, kStatusBadConfig);
+        }
         __syncwarp();
         const uint32_t dbytes = DELAYS ? uint32_t(se) * 32 : uint32_t(se) * P * 4;
         const uint32_t wbytes = WGT ? uint32_t(se) * 32 : 0u;
-        const uint32_t bytes = dbytes + wbytes + uint32_t(se4) * FB * 4 + wrows * FB * 4;
+        const uint32_t bytes = dbytes + wbytes + uint32_t(mcount) * FB * 4 + uint32_t(total_w) * FB * 4;
         if (lane == 0) {
           mbar_arrive_expect_tx(&full[st], bytes);
           const float* src = DELAYS ? d.anchor + (int64_t(q.tile) * d.n_sensors_pad + s0) * 8
@@ -368,8 +474,8 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
       }
       if (part & 2) {
         if (lane == 0)
-          bulk_g2s(sb + L.m, d.m + (int64_t(q.fg) * d.n_sensors_pad + s0) * FB,
-                   uint32_t(se4) * FB * 4, &full[st]);
+          bulk_g2s(sb + L.m, d.m + (int64_t(q.fg) * d.n_sensors_pad + ma) * FB,
+                   uint32_t(mcount) * FB * 4, &full[st]);
         if (wl > 0) {
           const unsigned char* src =
               static_cast<const unsigned char*>(d.b) +
@@ -377,6 +483,7 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
           bulk_g2s(sb + L.win + size_t(off) * FB * 4, src, uint32_t(wl) * FB * 4, &full[st]);
         }
       }
+      return se;
     };
     // the first unit of every CTA is blockIdx.x (no ticket round trip at the
     // start); later units come from the ticket, offset by the grid size
@@ -418,20 +525,19 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
         // still runs; its outputs (multipliers, windows) only after the wait
         const int64_t seq0 = seq;
         int k = 0;
-        for (int s = q.s_lo; s < q.s_hi && k < p.stages; s += p.S, ++k)
-          issue_chunk(q, d, mrow, s, int((seq0 + k) % p.stages), 1);
+        for (int s = q.s_lo; s < q.s_hi && k < p.stages; ++k)
+          s += issue_chunk(q, d, mrow, s, int((seq0 + k) % p.stages), 1);
         asm volatile("griddepcontrol.wait;" ::: "memory");
         waited_inputs = true;
-        for (int i = 0; i < k; ++i, s0 += p.S, ++seq)
-          issue_chunk(q, d, mrow, s0, int(seq % p.stages), 2);
+        for (int i = 0; i < k; ++i, ++seq) s0 += issue_chunk(q, d, mrow, s0, int(seq % p.stages), 2);
       }
-      for (; s0 < q.s_hi; s0 += p.S, ++seq) {
+      for (; s0 < q.s_hi; ++seq) {
         const int st = int(seq % p.stages);
         if (!acquire_stage(st)) {
           ok = false;
           break;
         }
-        issue_chunk(q, d, mrow, s0, st, 3);
+        s0 += issue_chunk(q, d, mrow, s0, st, 3);
       }
       t_cur = t_next;
       t_next = __shfl_sync(0xffffffffu, t_next2, 0);
@@ -472,6 +578,73 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
       const int64_t u = unit_ring[j % kRing];
       if (u < 0) break;
       const UnitPos q = decode_unit(p, u, inst);
+      if constexpr (FB == 16) {
+        // wide unit: lane (g, c) owns frames 4c..4c+3 of pixels g + 8 j
+        const int g = lane >> 2, c = lane & 3;
+        const int px = pg * 64 + g;
+        float4 pq[DELAYS || WGT ? 8 : 1];
+        if constexpr (DELAYS != 0 || WGT != 0) {
+          const float4* src = p.inst[q.inst].pix + int64_t(q.tile) * P + px;
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) pq[jj] = __ldcg(src + 8 * jj);
+        }
+        float acc[8][4];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) acc[jj][f] = 0.0f;
+        for (int s0 = q.s_lo; s0 < q.s_hi; ++seq) {
+          const int st = int(seq % p.stages);
+          if (s0 != q.s_lo && !wait_full(st)) {
+            ok = false;
+            break;
+          }
+          const int2 hdr = stage_hdr[st];
+          const int se = hdr.x;
+          // the first sensor of the stage whose phase in the segment is sp
+          const int sl0 = (sp - (s0 - q.s_lo)) & (SW - 1);
+          s0 += se;
+          const unsigned char* sb = stage0 + st * L.bytes;
+          const float* su = reinterpret_cast<const float*>(sb + L.u) + px;
+          const uint32_t* sm = reinterpret_cast<const uint32_t*>(sb + L.m) + hdr.y * FB;
+          const int* soff = reinterpret_cast<const int*>(sb + L.off);
+          const uint32_t* sw = reinterpret_cast<const uint32_t*>(sb + L.win);
+          const float4* swa = reinterpret_cast<const float4*>(sb + L.wa);
+          const float4* sa = reinterpret_cast<const float4*>(sb + L.u);
+          for (int sl = sl0; sl < se; sl += SW) {
+            float uu[8], ww[8];
+            if constexpr (DELAYS == 0) {
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) uu[jj] = su[sl * P + 8 * jj];
+            } else {
+              const float4 A = sa[2 * sl], B = sa[2 * sl + 1];
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) uu[jj] = const_delay(pq[jj], A, B);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) ww[jj] = 1.0f;
+            if constexpr (WGT != 0) {
+              const float4 E = swa[2 * sl], N = swa[2 * sl + 1];
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) ww[jj] = solid_angle_weight(pq[jj], E, N);
+            }
+            lerp_accumulate_wide<FMT, WGT>(acc, uu, ww, sm + sl * FB, soff[sl], sw, p.Wst, c);
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[st]);
+        }
+        if (!ok) break;
+        const int buf = int(j & 1);
+        if (j >= 2) red_free_sync(buf, (NWC + 1) * 32);
+        float* rb = red + size_t(buf) * SW * FB * P;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) rb[(sp * FB + 4 * c + f) * P + px + 8 * jj] = acc[jj][f];
+        if (threadIdx.x == 0) red_unit[buf] = u;
+        red_full_arrive(buf, (NWC + 1) * 32);
+        continue;
+      }
       float4 pq[4];  // constant speed or weights: the lane's pixels relative to the tile anchor
       if constexpr (DELAYS != 0 || WGT != 0) {
         const float4* src = p.inst[q.inst].pix + int64_t(q.tile) * P + pg * 128 + lane;
@@ -483,20 +656,25 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
       for (int fb = 0; fb < FB; ++fb)
 #pragma unroll
         for (int x = 0; x < 4; ++x) acc[fb][x] = 0.0f;
-      for (int s0 = q.s_lo; s0 < q.s_hi; s0 += p.S, ++seq) {
+      for (int s0 = q.s_lo; s0 < q.s_hi; ++seq) {
         const int st = int(seq % p.stages);
         if (s0 != q.s_lo && !wait_full(st)) {
           ok = false;
           break;
         }
-        const int se = min(p.S, q.s_hi - s0);
+        const int2 hdr = stage_hdr[st];  // sensors of the stage, multiplier shift
+        const int se = hdr.x;
+        // phase sp takes the sensors s with (s - s_lo) mod SW == sp, whatever
+        // sensor the stage starts at
+        const int sl0 = (sp - (s0 - q.s_lo)) & (SW - 1);
+        s0 += se;
         const unsigned char* sb = stage0 + st * L.bytes;
         const float* su = reinterpret_cast<const float*>(sb + L.u) + pg * 128 + lane;
-        const uint32_t* sm = reinterpret_cast<const uint32_t*>(sb + L.m);
+        const uint32_t* sm = reinterpret_cast<const uint32_t*>(sb + L.m) + hdr.y * FB;
         const int* soff = reinterpret_cast<const int*>(sb + L.off);
         const uint32_t* sw = reinterpret_cast<const uint32_t*>(sb + L.win);
         const float4* swa = reinterpret_cast<const float4*>(sb + L.wa);
-        int sl = sp;
+        int sl = sl0;
         if constexpr (DELAYS == 0) {
           for (; sl + SW < se; sl += 2 * SW) {
             gather_sensor<P, FB, FMT, WGT>(acc, su, sm, soff, sw, sl, p.Wst, pq, swa);
@@ -557,35 +735,43 @@ __global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB ==
       const int f0 = q.fg * FB;
       const int fb_eff = min(FB, d.n_frames - f0);
       const float* rb = red + size_t(ew) * SW * FB * P;
-      float v[FB][KO];
-#pragma unroll
-      for (int fb = 0; fb < FB; ++fb)
-#pragma unroll
-        for (int k = 0; k < KO; ++k) {
-          const int o = fb * P + k * 32 + lane;
-          float a = 0.0f;
-#pragma unroll
-          for (int ph = 0; ph < SW; ++ph) a += rb[ph * FB * P + o];  // fixed phase order
-          v[fb][k] = a;
-        }
-      red_free_arrive(ew, (NWC + 1) * 32);  // red[ew] free again
       int slot_idx[KO];
 #pragma unroll
       for (int k = 0; k < KO; ++k) slot_idx[k] = __ldcg(d.slot + int64_t(q.tile) * P + k * 32 + lane);
       const int64_t pbase = ((int64_t(q.fg) * d.n_tiles + q.tile) * d.n_seg) * FB * P;
-      if (d.n_seg == 1) {
-#pragma unroll
-        for (int fb = 0; fb < FB; ++fb)
-#pragma unroll
-          for (int k = 0; k < KO; ++k)
-            if (fb < fb_eff && slot_idx[k] >= 0) d.out[int64_t(f0 + fb) * d.out_stride + slot_idx[k]] = v[fb][k];
-        continue;
-      }
       float* mine = d.part + pbase + int64_t(q.seg) * FB * P;
+      // the unit's sums FC frames at a time (all of them when FB <= 8; 16
+      // frames of 8 outputs would take 128 registers)
+      constexpr int FC = FB > 8 ? 4 : FB;
 #pragma unroll
-      for (int fb = 0; fb < FB; ++fb)
+      for (int fc = 0; fc < FB; fc += FC) {
+        float v[FC][KO];
 #pragma unroll
-        for (int k = 0; k < KO; ++k) __stcg(mine + fb * P + k * 32 + lane, v[fb][k]);
+        for (int fb = 0; fb < FC; ++fb)
+#pragma unroll
+          for (int k = 0; k < KO; ++k) {
+            const int o = (fc + fb) * P + k * 32 + lane;
+            float a = 0.0f;
+#pragma unroll
+            for (int ph = 0; ph < SW; ++ph) a += rb[ph * FB * P + o];  // fixed phase order
+            v[fb][k] = a;
+          }
+        if (fc + FC == FB) red_free_arrive(ew, (NWC + 1) * 32);  // red[ew] free again
+        if (d.n_seg == 1) {
+#pragma unroll
+          for (int fb = 0; fb < FC; ++fb)
+#pragma unroll
+            for (int k = 0; k < KO; ++k)
+              if (fc + fb < fb_eff && slot_idx[k] >= 0)
+                d.out[int64_t(f0 + fc + fb) * d.out_stride + slot_idx[k]] = v[fb][k];
+        } else {
+#pragma unroll
+          for (int fb = 0; fb < FC; ++fb)
+#pragma unroll
+            for (int k = 0; k < KO; ++k) __stcg(mine + (fc + fb) * P + k * 32 + lane, v[fb][k]);
+        }
+      }
+      if (d.n_seg == 1) continue;
       // the last segment of a tile to finish sums all segments in fixed order;
       // the counter's release/acquire orders the partials of every lane (the
       // warp barrier before it makes the other lanes' stores part of the release)
@@ -638,7 +824,7 @@ static cudaError_t gather_t(const StreamParams& p, size_t smem, int grid, cudaSt
     if (e != cudaSuccess) return e;
     smem_set = smem;
   }
-  const int threads = 32 * ((P / 128) * SW + 3);
+  const int threads = 32 * (consumer_pixel_warps<P, FB>() * SW + 3);
   if (resident) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -667,6 +853,7 @@ static cudaError_t gather_fb(int FB, const StreamParams& p, size_t smem, int gri
     case 2: return gather_t<P, 2, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
     case 4: return gather_t<P, 4, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
     case 8: return gather_t<P, 8, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
+    case 16: return gather_t<P, 16, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -697,6 +884,7 @@ static const void* gather_func_fb(int FB) {
     case 2: return reinterpret_cast<const void*>(gather_kernel<P, 2, FMT, SW, MODE>);
     case 4: return reinterpret_cast<const void*>(gather_kernel<P, 4, FMT, SW, MODE>);
     case 8: return reinterpret_cast<const void*>(gather_kernel<P, 8, FMT, SW, MODE>);
+    case 16: return reinterpret_cast<const void*>(gather_kernel<P, 16, FMT, SW, MODE>);
   }
   return nullptr;
 }

@@ -50,8 +50,8 @@ struct pat_bp_s {
   int pre_fb = 1;                     // their frames per group
   int wst_cache[33] = {0};            // stage window bound per sensors-per-stage
   // launch shapes chosen by the autotuner: [frames-per-group index][format]
-  int tuned_S[4][3] = {};
-  int tuned_budget_kb[4][3] = {};
+  int tuned_S[5][3] = {};
+  int tuned_budget_kb[5][3] = {};
   float* d_u = nullptr;               // table offsets (delays == 0)
   float* d_anchor = nullptr;          // per (tile, sensor) anchors (delays == 1)
   float4* d_pix = nullptr;            // per-pixel terms (delays == 1 or wgt)
@@ -105,6 +105,8 @@ int fmt_for(pat_dtype dt);
 pat_status ensure_buffers_fb(pat_bp_t h, int n_frames, int FB);
 // window rows one pipeline stage of S sensors can need
 int stage_window(pat_bp_t h, int S);
+// stages and window-row budget of a shape under a smem budget (false: nothing fits)
+bool fit_stages(GatherConfig& c, int wmin, int wfull, size_t budget, int* wst);
 // launch shape: frames per unit, sensors per stage, stages under a smem budget
 GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst);
 GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst);

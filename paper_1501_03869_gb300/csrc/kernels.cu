@@ -173,25 +173,48 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
     }
   }
   uint32_t* dst = static_cast<uint32_t*>(p.b) + (int64_t(g) * p.n_sensors + s) * p.n_t_pad * FB;
+  // Rows of 16 frames are formed 8 frames at a time (registers), and their
+  // four 16-byte chunks are stored rotated as the gather's wide units read
+  // them: chunk c of row k sits at chunk c ^ ((k / 2) mod 4).  The runs start
+  // at multiples of 8 rows, so row k0 + j rotates by (j / 2) mod 4.
+  constexpr int FH = FB > 8 ? 8 : FB;
   for (int kw = (threadIdx.x & ~31) * K; kw < p.n_t_pad; kw += blockDim.x * K) {
     const int k0 = kw + lane * K;
-    uint32_t w[K * FB];
 #pragma unroll
-    for (int fb = 0; fb < FB; ++fb) {
-      if (fb < fb_eff) {
-        float b[K + 1];
-        b_run(fb, k0, b);
+    for (int h = 0; h < FB; h += FH) {
+      uint32_t w[K * FH];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-          if constexpr (FMT == kBF32) w[j * FB + fb] = __float_as_uint(b[j]);
-          else w[j * FB + fb] = encode_pair<FMT>(b[j] * inv[fb], b[j + 1] * inv[fb]);
+      for (int fl = 0; fl < FH; ++fl) {
+        const int fb = h + fl;
+        if (fb < fb_eff) {
+          float b[K + 1];
+          b_run(fb, k0, b);
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            if constexpr (FMT == kBF32) w[j * FH + fl] = __float_as_uint(b[j]);
+            else w[j * FH + fl] = encode_pair<FMT>(b[j] * inv[fb], b[j + 1] * inv[fb]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < K; ++j) w[j * FH + fl] = 0u;
         }
+      }
+      if (k0 >= p.n_t_pad) continue;
+      if constexpr (FB <= 8) {
+        store_words<K * FB>(dst + int64_t(k0) * FB, w);
       } else {
 #pragma unroll
-        for (int j = 0; j < K; ++j) w[j * FB + fb] = 0u;
+        for (int j = 0; j < K; ++j) {
+          const int rot = (j >> 1) & 3;
+          const int m = (h >> 3) ^ (rot >> 1);  // the 32-byte half this pass's two chunks go to
+          uint32_t* row = dst + (int64_t(k0) + j) * FB + 8 * m;
+          const uint4 a = make_uint4(w[j * 8 + 0], w[j * 8 + 1], w[j * 8 + 2], w[j * 8 + 3]);
+          const uint4 b4 = make_uint4(w[j * 8 + 4], w[j * 8 + 5], w[j * 8 + 6], w[j * 8 + 7]);
+          *reinterpret_cast<uint4*>(row) = (rot & 1) ? b4 : a;
+          *reinterpret_cast<uint4*>(row + 4) = (rot & 1) ? a : b4;
+        }
       }
     }
-    if (k0 < p.n_t_pad) store_words<K * FB>(dst + int64_t(k0) * FB, w);
   }
   if (threadIdx.x < FB) {
     const int fb = threadIdx.x;
@@ -252,7 +275,7 @@ __global__ void wait_probe_kernel(int* status, uint64_t timeout_ns) {
 }
 
 // --------------------------------------------------------------- launchers --
-int gather_threads(const GatherConfig& c) { return 32 * ((c.P / 128) * c.SW + 3); }
+int gather_threads(const GatherConfig& c) { return 32 * ((c.FB == 16 ? c.P / 64 : c.P / 128) * c.SW + 3); }
 
 size_t gather_smem_bytes(const GatherConfig& c, int Wst) {
   const StageLayout L(c.S, c.P, c.FB, Wst, c.delays | (c.wgt << 1));
@@ -267,6 +290,7 @@ static cudaError_t launch_pre_fb(const PreParams& p, cudaStream_t st) {
     case 2: preprocess_kernel<DT, FMT, 2><<<grid, 256, 0, st>>>(p); break;
     case 4: preprocess_kernel<DT, FMT, 4><<<grid, 256, 0, st>>>(p); break;
     case 8: preprocess_kernel<DT, FMT, 8><<<grid, 256, 0, st>>>(p); break;
+    case 16: preprocess_kernel<DT, FMT, 16><<<grid, 256, 0, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -282,6 +306,7 @@ static cudaError_t launch_pre_multi_fb(const PreMultiParams& p, cudaStream_t st)
     case 2: preprocess_multi_kernel<DT, FMT, 2><<<grid, 256, 0, st>>>(p); break;
     case 4: preprocess_multi_kernel<DT, FMT, 4><<<grid, 256, 0, st>>>(p); break;
     case 8: preprocess_multi_kernel<DT, FMT, 8><<<grid, 256, 0, st>>>(p); break;
+    case 16: preprocess_multi_kernel<DT, FMT, 16><<<grid, 256, 0, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -335,7 +360,7 @@ cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p,
   if (p.n_units == 0) return cudaSuccess;
   if (c.direct) {
     if (p.n_inst != 1) return cudaErrorInvalidValue;
-    return launch_gather_direct(c, fmt, p.inst[0], c.n_sm, p.status, p.host_status, st);
+    return launch_gather_direct(c, fmt, p.inst[0], c.n_sm, p.status, p.host_status, p.timeout_ns, st);
   }
   return gather_dispatch(c, fmt, p, grid, st, nullptr, 0);
 }
@@ -352,6 +377,7 @@ static const void* pre_multi_func_fb(int FB) {
     case 2: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 2>);
     case 4: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 4>);
     case 8: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 8>);
+    case 16: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 16>);
   }
   return nullptr;
 }

@@ -81,7 +81,7 @@ struct StreamParams {
 
 struct GatherConfig {
   int P = 128;      // pixels per tile
-  int FB = 1;       // frames per unit (1, 2, 4, 8)
+  int FB = 1;       // frames per unit (1, 2, 4, 8, 16)
   int SW = 4;       // sensor-phase warps
   int S = 16;       // sensors per stage
   int stages = 4;
@@ -111,7 +111,7 @@ cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t st)
 // kernel (c.FB == 1; d.part holds direct_part_floats floats); same arithmetic
 // and summation order as the staged kernel with one frame per unit.
 cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc& d, int n_sm,
-                                 const int* status, int* host_status,
+                                 int* status, int* host_status, uint64_t timeout_ns,
                                  cudaStream_t st);
 // Phase sums the unstaged gather stores (floats).
 size_t direct_part_floats(const GatherConfig& c, int n_tiles, int n_seg);

@@ -368,10 +368,10 @@ namespace patbp {
 int fmt_for(pat_dtype dt) { return dt == PAT_F32 ? kBF32 : (dt == PAT_BF16 ? kBBF16P : kBF16P); }
 
 int frames_per_group(int n_frames) {
-  return n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1));
+  return n_frames >= 16 ? 16 : (n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1)));
 }
 
-int fb_index(int FB) { return FB == 1 ? 0 : (FB == 2 ? 1 : (FB == 4 ? 2 : 3)); }
+int fb_index(int FB) { return FB == 1 ? 0 : (FB == 2 ? 1 : (FB == 4 ? 2 : (FB == 8 ? 3 : 4))); }
 
 static pat_status grow_zeroed(void** p, size_t* cap, size_t need, const char* what) {
   if (need <= *cap) return PAT_OK;
@@ -425,8 +425,32 @@ int stage_window(pat_bp_t h, int S) {
   return best;
 }
 
-// Launch shape under a shared-memory budget: as many stages as fit (2..6),
-// fewer sensors per stage if even two stages do not fit.
+// Stages and window-row budget of a launch shape under a shared-memory
+// budget.  A stage takes as many of its (at most S) sensors as fit the row
+// budget, so the budget must hold the longest single window (wmin) and never
+// needs more than the longest S-sensor sum (wfull).  The deepest pipeline (6
+// stages down to 3) whose row budget keeps at least half of wfull wins, else
+// two stages with whatever fits above wmin.  False if even that does not fit.
+bool fit_stages(GatherConfig& c, int wmin, int wfull, size_t budget, int* wst) {
+  for (c.stages = 6; c.stages >= 2; --c.stages) {
+    const size_t fixed = gather_smem_bytes(c, 0);       // everything but the window rows
+    const size_t per_row = size_t(c.stages) * c.FB * 4;  // one more row in every stage
+    if (fixed > budget) continue;
+    int w = int(std::min<size_t>((budget - fixed) / per_row, size_t(wfull)));
+    w &= ~7;
+    const int need = c.stages > 2 ? std::max(wmin, wfull / 2) : wmin;
+    if (w >= need) {
+      *wst = std::max(w, 8);
+      return true;
+    }
+  }
+  c.stages = 2;
+  *wst = wfull;
+  return false;
+}
+
+// Launch shape under a shared-memory budget: stages and row budget as
+// fit_stages decides; fewer sensors per stage if nothing fits.
 GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
   GatherConfig c;
   c.P = h->P;
@@ -436,11 +460,9 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
   c.n_sm = h->n_sm;
   c.FB = FB;
   c.S = S;
-  c.stages = 6;
+  const int wmin = stage_window(h, 1);
   for (;;) {
-    *wst = stage_window(h, c.S);
-    while (c.stages > 2 && gather_smem_bytes(c, *wst) > budget) --c.stages;
-    if (gather_smem_bytes(c, *wst) <= budget || c.S <= 4) break;
+    if (fit_stages(c, wmin, stage_window(h, c.S), budget, wst) || c.S <= 4) break;
     c.S = c.S > 8 ? c.S - 8 : 4;
   }
   return c;

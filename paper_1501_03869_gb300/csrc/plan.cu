@@ -1,12 +1,18 @@
-// plan.cu -- many instances in one persistent launch (include/pat_bp.h, plans).
+// plan.cu -- many instances in persistent launches (include/pat_bp.h, plans).
 //
-// Every instance (one speed map's table, Sec. III) contributes its units to
-// one gather launch; one preprocessing launch forms the Eq. (BP) integrand of
-// all instances first.  A plan can replay both launches as a CUDA graph whose
-// kernel-node parameters are refreshed per execution, and can time candidate
-// launch shapes once (autotuning).  None of the shape choices changes the
-// order in which a pixel's sensor terms are summed, so results never depend on
-// the shape, the graph or the other instances.
+// Every instance (one speed map's table, Sec. III) contributes its units of
+// work to a persistent gather launch.  Instances are grouped by the frames
+// that share one pass over a table tile (FB: the largest power of two up to
+// 16 not above the instance's frame count), and every group ("class") has its
+// own preprocessing launch (the Eq. (BP) integrand of all its instances) and
+// its own gather launch; all preprocessing launches go first, then the
+// gathers.  A 16-frame instance therefore streams its table once, while a
+// single-frame instance next to it does not pay for frames it does not have.
+// A plan can replay the launches as a CUDA graph whose kernel-node parameters
+// are refreshed per execution, and can time candidate launch shapes once
+// (autotuning).  None of the shape choices changes the order in which a
+// pixel's sensor terms are summed, so results never depend on the shape, the
+// classes, the graph or the other instances.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +30,24 @@
 
 using namespace patbp;
 
+namespace {
+
+// Instances of a plan that share frames per unit: one preprocessing and one
+// gather launch.
+struct PlanClass {
+  int FB = 1;
+  std::vector<int> idx;  // the plan's instance indices, in plan order
+  GatherConfig cfg;
+  int wst = 8;
+  int grid = 0;
+  int64_t n_units = 0;
+  std::unique_ptr<PreMultiParams> pre;
+  std::unique_ptr<StreamParams> gat;
+  cudaGraphNode_t pre_node = nullptr, gat_node = nullptr;
+};
+
+}  // namespace
+
 struct pat_plan_s {
   std::vector<pat_bp_t> hs;
   std::vector<int> frames;
@@ -31,105 +55,142 @@ struct pat_plan_s {
   int fmt = 0;
   unsigned flags = 0;
   int device = 0, n_sm = 0, P = 128, SW = 4;
-  // launch shape
-  int FB = 1, S = 16, budget_kb = 55;
-  GatherConfig cfg;
-  int wst = 8;
-  int grid = 0;
+  int fb_uniform = 0;  // 0: each instance's own frames per unit; else this for all
+  // launch shape shared by the classes
+  int S = 16, budget_kb = 55;
+  std::vector<PlanClass> cls;
   int64_t n_units = 0;
   bool tuned = false;
   double tune_ms = 0.0;
-  // device words owned by the plan
+  // device words owned by the plan (the gathers run one after the other and
+  // share them: the unit tickets return to zero at the end of every launch)
   int* d_status = nullptr;
   unsigned* d_sched = nullptr;
-  // parameter blocks (refreshed per execution)
-  std::unique_ptr<PreMultiParams> pre;
-  std::unique_ptr<StreamParams> gat;
   // graph
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t pre_node = nullptr, gat_node = nullptr;
   std::mutex mu;
 };
 
 namespace {
 
-pat_status plan_shape(pat_plan_t pl, int FB, int S, int budget_kb) {
-  pl->FB = FB;
+int instance_fb(pat_plan_t pl, int i) {
+  return pl->fb_uniform ? pl->fb_uniform : frames_per_group(pl->frames[i]);
+}
+
+// Classes and launch shapes for S sensors per stage under a shared-memory
+// budget of budget_kb per CTA.
+pat_status plan_shape(pat_plan_t pl, int S, int budget_kb) {
   pl->S = S;
   pl->budget_kb = budget_kb;
-  int wst = 8;
-  for (pat_bp_t h : pl->hs) wst = std::max(wst, stage_window(h, S));
-  // one shape for all instances: the largest stage window decides the stages
-  GatherConfig c;
-  c.P = pl->P;
-  c.SW = pl->SW;
-  c.delays = pl->hs[0]->delays;
-  c.wgt = pl->hs[0]->wgt;
-  c.FB = FB;
-  c.S = S;
-  c.stages = 6;
+  std::vector<int> fbs;
+  for (size_t i = 0; i < pl->hs.size(); ++i) fbs.push_back(instance_fb(pl, int(i)));
+  std::vector<int> order(fbs);
+  std::sort(order.begin(), order.end(), std::greater<int>());
+  order.erase(std::unique(order.begin(), order.end()), order.end());
+  std::vector<PlanClass> cls(order.size());
+  for (size_t c = 0; c < order.size(); ++c) {
+    cls[c].FB = order[c];
+    for (size_t i = 0; i < pl->hs.size(); ++i)
+      if (fbs[i] == order[c]) cls[c].idx.push_back(int(i));
+  }
   const size_t budget = std::min(size_t(budget_kb) * 1024, size_t(pl->hs[0]->max_smem));
-  while (c.stages > 2 && gather_smem_bytes(c, wst) > budget) --c.stages;
-  if (gather_smem_bytes(c, wst) > budget)
-    return fail(PAT_ERR_CUDA, "stage windows do not fit in shared memory for this shape");
-  pl->cfg = c;
-  pl->wst = wst;
-  for (size_t i = 0; i < pl->hs.size(); ++i) {
-    pat_status st = ensure_buffers_fb(pl->hs[i], pl->frames[i], FB);
-    if (st != PAT_OK) return st;
+  int64_t total_units = 0;
+  for (PlanClass& k : cls) {
+    // one shape per class: the longest single window and the longest
+    // S-sensor window sum of its instances bound the stages' row budget
+    int wmin = 8, wfull = 8;
+    for (int i : k.idx) {
+      wmin = std::max(wmin, stage_window(pl->hs[i], 1));
+      wfull = std::max(wfull, stage_window(pl->hs[i], S));
+    }
+    GatherConfig c;
+    c.P = pl->P;
+    c.SW = pl->SW;
+    c.delays = pl->hs[0]->delays;
+    c.wgt = pl->hs[0]->wgt;
+    c.FB = k.FB;
+    c.S = S;
+    int wst = wfull;
+    if (!fit_stages(c, wmin, wfull, budget, &wst))
+      return fail(PAT_ERR_CUDA, "stage windows do not fit in shared memory for this shape");
+    k.cfg = c;
+    k.wst = wst;
+    for (int i : k.idx) {
+      pat_status st = ensure_buffers_fb(pl->hs[i], pl->frames[i], k.FB);
+      if (st != PAT_OK) return st;
+    }
+    k.pre.reset(new (std::nothrow) PreMultiParams());
+    k.gat.reset(new (std::nothrow) StreamParams());
+    if (!k.pre || !k.gat) return fail(PAT_ERR_OOM, "plan parameters");
+    StreamParams& sp = *k.gat;
+    PreMultiParams& pm = *k.pre;
+    std::memset(&sp, 0, sizeof(sp));
+    std::memset(&pm, 0, sizeof(pm));
+    int64_t units = 0, ctas = 0;
+    for (size_t j = 0; j < k.idx.size(); ++j) {
+      pat_bp_t h = pl->hs[k.idx[j]];
+      const int F = pl->frames[k.idx[j]];
+      sp.inst[j] = make_desc(h, nullptr, F, k.FB, wst);
+      sp.inst[j].unit_begin = units;
+      units += int64_t(sp.inst[j].n_fg) * sp.inst[j].n_tiles * sp.inst[j].n_seg;
+      pm.inst[j] = make_pre(h, nullptr, pl->dtype, nullptr, F, k.FB);
+      pm.cta_begin[j] = ctas;
+      ctas += int64_t(h->ns) * sp.inst[j].n_fg;
+    }
+    if (ctas > 0x7fffffff) return fail(PAT_ERR_INVALID, "too many preprocessing rows in one plan");
+    pm.cta_begin[k.idx.size()] = ctas;
+    pm.n_inst = int(k.idx.size());
+    pm.dtype = int(pl->dtype);
+    pm.fmt = pl->fmt;
+    pm.FB = k.FB;
+    sp.n_inst = int(k.idx.size());
+    sp.n_units = units;
+    sp.S = c.S;
+    sp.stages = c.stages;
+    sp.Wst = wst;
+    sp.status = pl->d_status;
+    sp.sched = pl->d_sched;
+    sp.timeout_ns = 2000000000ull;
+    k.n_units = units;
+    total_units += units;
+    const int res = resident_ctas(c, pl->fmt, wst, pl->n_sm);
+    if (res <= 0) return fail(PAT_ERR_CUDA, "gather kernel does not fit on the device");
+    k.grid = int(std::min<int64_t>(std::max<int64_t>(units, 1), res));
   }
-  // unit ranges and preprocessing CTA ranges
-  StreamParams& sp = *pl->gat;
-  PreMultiParams& pm = *pl->pre;
-  std::memset(&sp, 0, sizeof(sp));
-  std::memset(&pm, 0, sizeof(pm));
-  int64_t units = 0, ctas = 0;
-  for (size_t i = 0; i < pl->hs.size(); ++i) {
-    pat_bp_t h = pl->hs[i];
-    sp.inst[i] = make_desc(h, nullptr, pl->frames[i], FB, wst);
-    sp.inst[i].unit_begin = units;
-    units += int64_t(sp.inst[i].n_fg) * sp.inst[i].n_tiles * sp.inst[i].n_seg;
-    pm.inst[i] = make_pre(h, nullptr, pl->dtype, nullptr, pl->frames[i], FB);
-    pm.cta_begin[i] = ctas;
-    ctas += int64_t(h->ns) * sp.inst[i].n_fg;
-  }
-  pm.cta_begin[pl->hs.size()] = ctas;
-  pm.n_inst = int(pl->hs.size());
-  pm.dtype = int(pl->dtype);
-  pm.fmt = pl->fmt;
-  pm.FB = FB;
-  sp.n_inst = int(pl->hs.size());
-  sp.n_units = units;
-  sp.S = pl->cfg.S;
-  sp.stages = pl->cfg.stages;
-  sp.Wst = wst;
-  sp.status = pl->d_status;
-  sp.sched = pl->d_sched;
-  sp.timeout_ns = 2000000000ull;
-  pl->n_units = units;
-  const int res = resident_ctas(pl->cfg, pl->fmt, wst, pl->n_sm);
-  if (res <= 0) return fail(PAT_ERR_CUDA, "gather kernel does not fit on the device");
-  pl->grid = int(std::min<int64_t>(units, res));
-  if (ctas > 0x7fffffff) return fail(PAT_ERR_INVALID, "too many preprocessing rows in one plan");
+  pl->cls = std::move(cls);
+  pl->n_units = total_units;
   return PAT_OK;
 }
 
 void fill_pointers(pat_plan_t pl, const void* const* sig, const float* const* scales,
                    float* const* outs) {
-  for (size_t i = 0; i < pl->hs.size(); ++i) {
-    pl->pre->inst[i].sig = sig[i];
-    pl->pre->inst[i].scales = scales ? scales[i] : nullptr;
-    pl->gat->inst[i].out = outs[i];
-  }
+  for (PlanClass& k : pl->cls)
+    for (size_t j = 0; j < k.idx.size(); ++j) {
+      const int i = k.idx[j];
+      k.pre->inst[j].sig = sig[i];
+      k.pre->inst[j].scales = scales ? scales[i] : nullptr;
+      k.gat->inst[j].out = outs[i];
+    }
 }
 
-pat_status launch_both(pat_plan_t pl, cudaStream_t st) {
-  cudaError_t e = launch_preprocess_multi(*pl->pre, st);
-  if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
-  e = launch_gather(pl->cfg, pl->fmt, *pl->gat, pl->grid, st);
-  if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+// All preprocessing launches, then all gathers.  A gather is a programmatic
+// dependent of the launch before it; the first waits for the last
+// preprocessing grid, whose stream predecessors (the other preprocessing
+// grids) are complete by then, and every later gather starts after the
+// gather before it has finished.
+pat_status launch_all(pat_plan_t pl, cudaStream_t st) {
+  for (PlanClass& k : pl->cls) {
+    if (k.n_units == 0) continue;
+    cudaError_t e = launch_preprocess_multi(*k.pre, st);
+    if (e != cudaSuccess) return cuda_fail(e, "preprocess launch");
+  }
+  for (PlanClass& k : pl->cls) {
+    if (k.n_units == 0) continue;
+    cudaError_t e = launch_gather(k.cfg, pl->fmt, *k.gat, k.grid, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+  }
   return PAT_OK;
 }
 
@@ -138,12 +199,8 @@ void drop_graph(pat_plan_t pl) {
   if (pl->graph) cudaGraphDestroy(pl->graph);
   pl->exec = nullptr;
   pl->graph = nullptr;
-  pl->pre_node = pl->gat_node = nullptr;
+  for (PlanClass& k : pl->cls) k.pre_node = k.gat_node = nullptr;
 }
-
-}  // namespace
-
-namespace {
 
 // Point every descriptor at the handles' current buffers: a handle's own
 // calls may have grown its working buffers since the plan was shaped, and an
@@ -151,36 +208,41 @@ namespace {
 // is taken again.  A handle whose kernel mode changed since (solid-angle
 // weights set) no longer fits the plan's launch shape.
 pat_status refresh_buffers(pat_plan_t pl) {
-  for (size_t i = 0; i < pl->hs.size(); ++i) {
-    pat_bp_t h = pl->hs[i];
-    if (h->evicted) return fail(PAT_ERR_INVALID, "a plan handle's table is evicted");
-    if (h->wgt != pl->cfg.wgt || h->delays != pl->cfg.delays)
-      return fail(PAT_ERR_INVALID, "a plan handle changed its weights since the plan was made");
-    pat_status st = ensure_buffers_fb(h, pl->frames[i], pl->FB);
-    if (st != PAT_OK) return st;
-    pl->pre->inst[i].weights = h->d_w;
-    pl->pre->inst[i].b = h->d_b;
-    pl->pre->inst[i].m = h->d_m;
-    InstDesc& d = pl->gat->inst[i];
-    d.u = h->d_u;
-    d.anchor = h->d_anchor;
-    d.pix = h->d_pix;
-    d.wanchor = h->wgt ? h->d_wanchor : nullptr;
-    d.base = h->d_base;
-    d.slot = h->d_slot;
-    d.zero_runs = h->d_zero_runs;
-    d.b = h->d_b;
-    d.m = h->d_m;
-    d.part = h->d_part;
-    d.counter = h->d_counter;
-  }
+  for (PlanClass& k : pl->cls)
+    for (size_t j = 0; j < k.idx.size(); ++j) {
+      const int i = k.idx[j];
+      pat_bp_t h = pl->hs[i];
+      if (h->evicted) return fail(PAT_ERR_INVALID, "a plan handle's table is evicted");
+      if (h->wgt != k.cfg.wgt || h->delays != k.cfg.delays)
+        return fail(PAT_ERR_INVALID, "a plan handle changed its weights since the plan was made");
+      pat_status st = ensure_buffers_fb(h, pl->frames[i], k.FB);
+      if (st != PAT_OK) return st;
+      k.pre->inst[j].weights = h->d_w;
+      k.pre->inst[j].b = h->d_b;
+      k.pre->inst[j].m = h->d_m;
+      InstDesc& d = k.gat->inst[j];
+      d.u = h->d_u;
+      d.anchor = h->d_anchor;
+      d.pix = h->d_pix;
+      d.wanchor = h->wgt ? h->d_wanchor : nullptr;
+      d.base = h->d_base;
+      d.slot = h->d_slot;
+      d.zero_runs = h->d_zero_runs;
+      d.b = h->d_b;
+      d.m = h->d_m;
+      d.part = h->d_part;
+      d.counter = h->d_counter;
+    }
   return PAT_OK;
 }
 
+// Capture the launches once; the graph's kernel nodes are told apart by their
+// parameter blocks (two classes can share a kernel), which equal the classes'
+// blocks at capture time.
 pat_status capture(pat_plan_t pl) {
   if (!pl->cap_stream) PAT_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
   PAT_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
-  pat_status st = launch_both(pl, pl->cap_stream);
+  pat_status st = launch_all(pl, pl->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
   if (st != PAT_OK) {
@@ -192,49 +254,60 @@ pat_status capture(pat_plan_t pl) {
   PAT_CUDA(cudaGraphGetNodes(g, nullptr, &n));
   std::vector<cudaGraphNode_t> nodes(n);
   PAT_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
-  const void* fpre = preprocess_multi_func(int(pl->dtype), pl->fmt, pl->FB);
-  const void* fgat = gather_kernel_func(pl->cfg, pl->fmt);
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType t;
     PAT_CUDA(cudaGraphNodeGetType(nd, &t));
     if (t != cudaGraphNodeTypeKernel) continue;
     cudaKernelNodeParams kp;
     PAT_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
-    if (kp.func == fpre) pl->pre_node = nd;
-    if (kp.func == fgat) pl->gat_node = nd;
+    if (!kp.kernelParams || !kp.kernelParams[0]) continue;
+    for (PlanClass& k : pl->cls) {
+      if (kp.func == preprocess_multi_func(int(pl->dtype), pl->fmt, k.FB) &&
+          std::memcmp(kp.kernelParams[0], k.pre.get(), sizeof(PreMultiParams)) == 0)
+        k.pre_node = nd;
+      if (kp.func == gather_kernel_func(k.cfg, pl->fmt) &&
+          std::memcmp(kp.kernelParams[0], k.gat.get(), sizeof(StreamParams)) == 0)
+        k.gat_node = nd;
+    }
   }
-  if (!pl->pre_node || !pl->gat_node) {
-    cudaGraphDestroy(g);
-    return fail(PAT_ERR_CUDA, "captured graph lacks the expected kernels");
-  }
+  for (PlanClass& k : pl->cls)
+    if (k.n_units > 0 && (!k.pre_node || !k.gat_node)) {
+      cudaGraphDestroy(g);
+      for (PlanClass& c : pl->cls) c.pre_node = c.gat_node = nullptr;
+      return fail(PAT_ERR_CUDA, "captured graph lacks the expected kernels");
+    }
   pl->graph = g;
   PAT_CUDA(cudaGraphInstantiate(&pl->exec, g, 0));
   return PAT_OK;
 }
 
 pat_status refresh_graph(pat_plan_t pl) {
-  void* pre_args[1] = {pl->pre.get()};
-  void* gat_args[1] = {pl->gat.get()};
-  cudaKernelNodeParams kp;
-  PAT_CUDA(cudaGraphKernelNodeGetParams(pl->pre_node, &kp));
-  kp.kernelParams = pre_args;
-  kp.extra = nullptr;
-  PAT_CUDA(cudaGraphExecKernelNodeSetParams(pl->exec, pl->pre_node, &kp));
-  PAT_CUDA(cudaGraphKernelNodeGetParams(pl->gat_node, &kp));
-  kp.kernelParams = gat_args;
-  kp.extra = nullptr;
-  PAT_CUDA(cudaGraphExecKernelNodeSetParams(pl->exec, pl->gat_node, &kp));
+  for (PlanClass& k : pl->cls) {
+    if (k.n_units == 0) continue;
+    void* pre_args[1] = {k.pre.get()};
+    void* gat_args[1] = {k.gat.get()};
+    cudaKernelNodeParams kp;
+    PAT_CUDA(cudaGraphKernelNodeGetParams(k.pre_node, &kp));
+    kp.kernelParams = pre_args;
+    kp.extra = nullptr;
+    PAT_CUDA(cudaGraphExecKernelNodeSetParams(pl->exec, k.pre_node, &kp));
+    PAT_CUDA(cudaGraphKernelNodeGetParams(k.gat_node, &kp));
+    kp.kernelParams = gat_args;
+    kp.extra = nullptr;
+    PAT_CUDA(cudaGraphExecKernelNodeSetParams(pl->exec, k.gat_node, &kp));
+  }
   return PAT_OK;
 }
 
 // Shapes chosen earlier in this process (and, with PAT_TUNE_CACHE set, in a
-// text file of "signature FB S budget_kb" lines), keyed by the plan's shape.
+// text file of "signature S budget_kb" lines), keyed by the plan's shape.
 std::mutex g_tune_mu;
 std::map<std::string, std::vector<int>> g_tune;
 
-std::string signature(pat_plan_t pl, bool fixed_fb) {
+std::string signature(pat_plan_t pl) {
   std::string s = "sm" + std::to_string(pl->n_sm) + ".dt" + std::to_string(int(pl->dtype)) +
-                  (fixed_fb ? ".fb" + std::to_string(pl->FB) : std::string(".fbany"));
+                  ".fb" + std::to_string(pl->fb_uniform) + ".w" + std::to_string(pl->hs[0]->wgt) +
+                  ".d" + std::to_string(pl->hs[0]->delays);
   for (size_t i = 0; i < pl->hs.size(); ++i) {
     pat_bp_t h = pl->hs[i];
     s += "|" + std::to_string(h->ns) + "x" + std::to_string(h->nt) + "x" + std::to_string(h->n_tiles) +
@@ -252,43 +325,34 @@ void tune_file_load() {
   FILE* f = std::fopen(path, "r");
   if (!f) return;
   char key[4096];
-  int fb, s, b;
-  while (std::fscanf(f, "%4095s %d %d %d", key, &fb, &s, &b) == 4) g_tune[key] = {fb, s, b};
+  int s, b;
+  while (std::fscanf(f, "%4095s %d %d", key, &s, &b) == 3) g_tune[key] = {s, b};
   std::fclose(f);
 }
 
-void tune_file_store(const std::string& key, int fb, int s, int b) {
+void tune_file_store(const std::string& key, int s, int b) {
   const char* path = std::getenv("PAT_TUNE_CACHE");
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d\n", key.c_str(), fb, s, b);
+  std::fprintf(f, "%s %d %d\n", key.c_str(), s, b);
   std::fclose(f);
 }
 
-// Times every candidate shape on the given inputs and keeps the fastest.
+// Times every candidate shape (sensors per stage x shared-memory budget) on
+// the given inputs and keeps the fastest; the frames per unit of every
+// instance follow from its frame count.
 pat_status autotune(pat_plan_t pl, const void* const* sig, const float* const* scales,
-                    float* const* outs, cudaStream_t st, bool fixed_fb) {
-  const std::string key = signature(pl, fixed_fb);
+                    float* const* outs, cudaStream_t st) {
+  const std::string key = signature(pl);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_file_load();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      pat_status s = plan_shape(pl, it->second[0], it->second[1], it->second[2]);
+      pat_status s = plan_shape(pl, it->second[0], it->second[1]);
       if (s == PAT_OK) pl->tuned = true;
       return s;
-    }
-  }
-  int max_f = 1;
-  for (int f : pl->frames) max_f = std::max(max_f, f);
-  std::vector<int> fbs;
-  if (fixed_fb) {
-    fbs.push_back(pl->FB);
-  } else {
-    for (int fb = 1; fb <= 8; fb *= 2) {
-      fbs.push_back(fb);
-      if (fb >= max_f) break;
     }
   }
   const int Ss[4] = {4, 8, 16, 32};
@@ -297,58 +361,56 @@ pat_status autotune(pat_plan_t pl, const void* const* sig, const float* const* s
   PAT_CUDA(cudaEventCreate(&e0));
   PAT_CUDA(cudaEventCreate(&e1));
   double best = 1e30;
-  int bfb = pl->FB, bs = pl->S, bb = pl->budget_kb;
+  int bs = pl->S, bb = pl->budget_kb;
   pat_status st_all = PAT_OK;
-  for (int fb : fbs)
-    for (int S : Ss)
-      for (int b : budgets) {
-        if (S == 4 && b != budgets[3]) continue;  // 4 sensors per stage only as a last resort
-        pat_status s = plan_shape(pl, fb, S, b);
-        if (s != PAT_OK) continue;
-        if ((s = refresh_buffers(pl)) != PAT_OK) {
-          st_all = s;
-          continue;
-        }
-        fill_pointers(pl, sig, scales, outs);
-        if (launch_both(pl, st) != PAT_OK) continue;  // warm-up
-        float ms = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {  // best of three
-          cudaEventRecord(e0, st);
-          if (launch_both(pl, st) != PAT_OK) break;
-          cudaEventRecord(e1, st);
-          if (cudaEventSynchronize(e1) != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return cuda_fail(cudaGetLastError(), "autotune run");
-          }
-          float t = 0.0f;
-          cudaEventElapsedTime(&t, e0, e1);
-          ms = std::min(ms, t);
-        }
-        if (ms < best) {
-          best = ms;
-          bfb = fb;
-          bs = S;
-          bb = b;
-        }
+  for (int S : Ss)
+    for (int b : budgets) {
+      if (S == 4 && b != budgets[3]) continue;  // 4 sensors per stage only as a last resort
+      pat_status s = plan_shape(pl, S, b);
+      if (s != PAT_OK) continue;
+      if ((s = refresh_buffers(pl)) != PAT_OK) {
+        st_all = s;
+        continue;
       }
+      fill_pointers(pl, sig, scales, outs);
+      if (launch_all(pl, st) != PAT_OK) continue;  // warm-up
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {  // best of three
+        cudaEventRecord(e0, st);
+        if (launch_all(pl, st) != PAT_OK) break;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return cuda_fail(cudaGetLastError(), "autotune run");
+        }
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (ms < best) {
+        best = ms;
+        bs = S;
+        bb = b;
+      }
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best >= 1e30) return st_all != PAT_OK ? st_all : fail(PAT_ERR_CUDA, "no launch shape ran");
-  pat_status s = plan_shape(pl, bfb, bs, bb);
+  pat_status s = plan_shape(pl, bs, bb);
   if (s != PAT_OK) return s;
   pl->tuned = true;
   pl->tune_ms = best;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = {bfb, bs, bb};
-  tune_file_store(key, bfb, bs, bb);
+  g_tune[key] = {bs, bb};
+  tune_file_store(key, bs, bb);
   return PAT_OK;
 }
 
 }  // namespace
 
 static pat_status plan_new(const pat_bp_t* handles, const int* n_frames, int n, pat_dtype dtype,
-                           unsigned flags, bool own_words, pat_plan_t* out) {
+                           unsigned flags, bool own_words, int fb_uniform, pat_plan_t* out) {
   if (!out) return fail(PAT_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!handles || !n_frames || n < 1 || n > kMaxInst)
@@ -379,9 +441,7 @@ static pat_status plan_new(const pat_bp_t* handles, const int* n_frames, int n, 
   pl->n_sm = handles[0]->n_sm;
   pl->P = handles[0]->P;
   pl->SW = handles[0]->SW;
-  pl->pre.reset(new (std::nothrow) PreMultiParams());
-  pl->gat.reset(new (std::nothrow) StreamParams());
-  if (!pl->pre || !pl->gat) return fail(PAT_ERR_OOM, "plan parameters");
+  pl->fb_uniform = fb_uniform;
   PAT_CUDA(cudaSetDevice(pl->device));
   if (own_words) {
     if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess ||
@@ -395,19 +455,14 @@ static pat_status plan_new(const pat_bp_t* handles, const int* n_frames, int n, 
     pl->d_status = handles[0]->d_status;
     pl->d_sched = handles[0]->d_sched;
   }
-  std::vector<int> fr(pl->frames);
-  std::sort(fr.begin(), fr.end());
-  // default shape: frames per unit from the median frame count; if the stage
-  // windows do not fit, fewer sensors per stage, more shared memory, then
-  // fewer frames per unit
+  // default shape: 8 sensors per stage in 100 KB; if the stage windows do not
+  // fit, the device's limit, then 4 sensors per stage
   pat_status st = PAT_ERR_CUDA;
   const int limit_kb = handles[0]->max_smem / 1024;
-  for (int FB = frames_per_group(fr[fr.size() / 2]); FB >= 1 && st != PAT_OK; FB /= 2) {
-    const int tries[3][2] = {{FB == 1 ? 16 : 8, FB == 1 ? 55 : 100}, {8, limit_kb}, {4, limit_kb}};
-    for (const auto& t : tries) {
-      st = plan_shape(pl.get(), FB, t[0], t[1]);
-      if (st == PAT_OK) break;
-    }
+  const int tries[3][2] = {{8, 100}, {8, limit_kb}, {4, limit_kb}};
+  for (const auto& t : tries) {
+    st = plan_shape(pl.get(), t[0], t[1]);
+    if (st == PAT_OK) break;
   }
   if (st != PAT_OK) {
     if (own_words) {
@@ -447,12 +502,12 @@ static pat_status plan_run(pat_plan_t pl, const void* const* sig, const float* c
   const HandleLocks locks(pl->hs);
   pat_status st;
   if ((pl->flags & PAT_PLAN_AUTOTUNE) && !pl->tuned) {
-    if ((st = autotune(pl, sig, scales, outs, stream, false)) != PAT_OK) return st;
     drop_graph(pl);
+    if ((st = autotune(pl, sig, scales, outs, stream)) != PAT_OK) return st;
   }
   if ((st = refresh_buffers(pl)) != PAT_OK) return st;
   fill_pointers(pl, sig, scales, outs);
-  if (!(pl->flags & PAT_PLAN_GRAPH)) return launch_both(pl, stream);
+  if (!(pl->flags & PAT_PLAN_GRAPH)) return launch_all(pl, stream);
   if (!pl->exec) {
     if ((st = capture(pl)) != PAT_OK) return st;
   } else if ((st = refresh_graph(pl)) != PAT_OK) {
@@ -477,7 +532,8 @@ static void plan_free(pat_plan_t pl) {
 
 extern "C" pat_status pat_plan_create(const pat_bp_t* handles, const int* n_frames, int n,
                                       pat_dtype dtype, unsigned flags, pat_plan_t* out) {
-  return plan_new(handles, n_frames, n, dtype, flags & (PAT_PLAN_AUTOTUNE | PAT_PLAN_GRAPH), true, out);
+  return plan_new(handles, n_frames, n, dtype, flags & (PAT_PLAN_AUTOTUNE | PAT_PLAN_GRAPH), true, 0,
+                  out);
 }
 
 extern "C" pat_status pat_plan_execute(pat_plan_t plan, const void* const* signals_dev,
@@ -506,16 +562,21 @@ extern "C" pat_status pat_plan_sync(pat_plan_t plan, pat_stream_t stream) {
 extern "C" pat_status pat_plan_info(pat_plan_t plan, pat_plan_info_t* info) {
   if (!plan || !info) return fail(PAT_ERR_INVALID, "NULL argument");
   std::lock_guard<std::mutex> lk(plan->mu);
+  std::memset(info, 0, sizeof(*info));
   info->n_inst = int(plan->hs.size());
-  info->frames_per_unit = plan->FB;
-  info->sensors_per_stage = plan->cfg.S;
-  info->stages = plan->cfg.stages;
+  info->sensors_per_stage = plan->S;
   info->smem_budget_kb = plan->budget_kb;
-  info->grid = plan->grid;
   info->n_units = plan->n_units;
   info->tuned = plan->tuned ? 1 : 0;
   info->graph = plan->exec ? 1 : 0;
   info->tune_ms = plan->tune_ms;
+  info->n_classes = int(plan->cls.size());
+  for (const PlanClass& k : plan->cls) {
+    info->frames_per_unit = std::max(info->frames_per_unit, k.FB);
+    info->stages = std::max(info->stages, k.cfg.stages);
+    info->grid = std::max(info->grid, k.grid);
+    info->fb_mask |= k.FB;
+  }
   return PAT_OK;
 }
 
@@ -529,7 +590,7 @@ extern "C" pat_status pat_bp_reconstruct_multi(const pat_bp_t* handles, const vo
                                                const int* n_frames, float* const* outs_dev, int n,
                                                pat_stream_t stream) {
   pat_plan_t pl = nullptr;
-  pat_status st = plan_new(handles, n_frames, n, dtype, 0, false, &pl);
+  pat_status st = plan_new(handles, n_frames, n, dtype, 0, false, 0, &pl);
   if (st != PAT_OK) return st;
   st = plan_run(pl, signals_dev, scales_dev, outs_dev, static_cast<cudaStream_t>(stream));
   // the plan's parameter blocks were copied at launch; its device words are
@@ -545,16 +606,15 @@ extern "C" pat_status pat_bp_autotune(pat_bp_t h, const void* signals_dev, pat_d
   if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
   std::lock_guard<std::mutex> lk(h->mu);
   pat_plan_t pl = nullptr;
-  pat_status st = plan_new(&h, &n_frames, 1, dtype, 0, false, &pl);
+  pat_status st = plan_new(&h, &n_frames, 1, dtype, 0, false, frames_per_group(n_frames), &pl);
   if (st != PAT_OK) return st;
-  pl->FB = frames_per_group(n_frames);
   const void* sig[1] = {signals_dev};
   const float* sc[1] = {scales_dev};
   float* outs[1] = {out_dev};
   st = autotune(pl, sig, dtype == PAT_F32 ? (scales_dev ? sc : nullptr) : sc, outs,
-                static_cast<cudaStream_t>(stream), true);
+                static_cast<cudaStream_t>(stream));
   if (st == PAT_OK) {
-    const int fi = fb_index(pl->FB);
+    const int fi = fb_index(pl->fb_uniform);
     h->tuned_S[fi][pl->fmt] = pl->S;
     h->tuned_budget_kb[fi][pl->fmt] = pl->budget_kb;
   }

@@ -47,6 +47,10 @@ def test_plan_tuned_graph_matches_single_handles(c4):
     plan.sync()
     info = plan.info
     assert info["tuned"] == 1 and info["graph"] == 1 and info["n_inst"] == 32
+    # one class per frames-per-unit value the instances' frame counts give
+    fbs = {min(16, 1 << (w.n_frames.bit_length() - 1)) for w in ws}
+    assert info["n_classes"] == len(fbs) and info["fb_mask"] == sum(fbs)
+    assert info["frames_per_unit"] == max(fbs)
     for i, o in enumerate(outs):
         assert np.array_equal(o.cpu().numpy(), single[i]), f"instance {i}"
     # replay with other inputs: every pointer is refreshed in the graph
