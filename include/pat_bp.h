@@ -282,23 +282,26 @@ pat_status pat_table_host(const float* speed_host, const pat_grid* grid, const d
                           int32_t* slot_host);
 
 /* ------------------------------------------------------------------------
- * Many instances in one persistent launch (uneven grids, sensor counts,
- * sample counts and frame counts).  A plan fixes the handles and their frame
- * counts; each execution streams the preprocessing of every instance in one
- * launch and the back projection of every instance in one persistent gather
- * launch (programmatically dependent on the first), optionally as a CUDA
- * graph.  The summation order of every instance is its handle's own, so each
- * image is bit-identical to that handle's pat_bp_reconstruct of the same
- * frames, whatever else is in the plan or however the launch is shaped.
+ * Many instances in persistent launches (uneven grids, sensor counts, sample
+ * counts and frame counts).  A plan fixes the handles and their frame counts
+ * and groups the instances by frames per unit FB (the largest power of two up
+ * to 16 not above an instance's frame count: FB frames share each pass over a
+ * table tile).  Each execution runs one preprocessing launch per group, then
+ * one persistent gather launch per group (the first programmatically
+ * dependent on the preprocessing), optionally replayed as a CUDA graph.  The
+ * summation order of every instance is its handle's own, so each image is
+ * bit-identical to that handle's pat_bp_reconstruct of the same frames,
+ * whatever else is in the plan or however the launches are shaped.
  * ------------------------------------------------------------------------ */
 typedef struct pat_plan_s* pat_plan_t;
 
 #define PAT_PLAN_AUTOTUNE 0x1u /* time candidate launch shapes at the first execution */
-#define PAT_PLAN_GRAPH 0x2u    /* capture the two launches once, replay a CUDA graph */
+#define PAT_PLAN_GRAPH 0x2u    /* capture the launches once, replay a CUDA graph */
 
 typedef struct {
   int n_inst;
-  int frames_per_unit;   /* FB: frames that share one pass over a table tile  */
+  int frames_per_unit;   /* FB: frames that share one pass over a table tile
+                            (the largest over the plan's classes)              */
   int sensors_per_stage; /* S                                                  */
   int stages;            /* pipeline depth of the gather                       */
   int smem_budget_kb;    /* shared memory per CTA the shape was sized for      */
@@ -307,6 +310,9 @@ typedef struct {
   int tuned;             /* 1 once the autotuner chose the shape               */
   int graph;             /* 1 once a CUDA graph is captured                    */
   double tune_ms;        /* best measured time per execution while tuning      */
+  int n_classes;         /* groups of instances with the same FB (one
+                            preprocessing and one gather launch each)          */
+  int fb_mask;           /* OR of the classes' FB values                       */
 } pat_plan_info_t;
 
 /* pat_plan_create -- n (1..64) distinct handles of one device, all with the
@@ -406,8 +412,25 @@ pat_status pat_srv_poll(pat_srv_t srv, uint64_t ticket, int timeout_us, double* 
 
 pat_status pat_srv_stats(pat_srv_t srv, pat_srv_stats_t* stats);
 
+/* pat_srv_set_budget -- change the HBM budget of a running server (bytes > 0).
+ * Idle resident subjects are evicted to their host copies, least recently
+ * used first, until the resident ones fit; subjects with batches in flight
+ * stay until those finish, and later admissions keep to the new budget.
+ * Blocking (an eviction waits for the device).  PAT_ERR_INVALID for a zero
+ * budget. */
+pat_status pat_srv_set_budget(pat_srv_t srv, size_t hbm_budget);
+
 /* pat_srv_destroy -- finish everything in flight, stop the scheduler, free. */
 pat_status pat_srv_destroy(pat_srv_t srv);
+
+/* pat_probe_l2_to_smem -- diagnostic (no counterpart in the paper): measures,
+ * on the current device, the aggregate bandwidth of 1-D bulk copies from an
+ * L2-resident buffer into shared memory (one CTA per SM streaming 64 KB
+ * chunks of a 64 MB buffer through three slots, about 2 GB), the path the
+ * staged gather's table blocks and integrand windows take.  Writes GB/s to
+ * *gbps.  Allocates and frees 64 MB of device memory; synchronous.  Errors:
+ * PAT_ERR_INVALID, PAT_ERR_CUDA, PAT_ERR_TIMEOUT (a bounded wait gave up). */
+pat_status pat_probe_l2_to_smem(double* gbps);
 
 /* pat_test_wait_timeout -- launches one CTA whose mbarrier wait can never
  * complete, bounded by timeout_ns; returns PAT_ERR_TIMEOUT when the kernel

@@ -23,7 +23,7 @@ from . import _lib
 from ._lib import PatError
 
 __all__ = ["BP", "Plan", "Server", "PatError", "fmm_host", "fmm_gpu", "table_host", "reconstruct_multi",
-           "wait_timeout_probe", "DTYPES"]
+           "wait_timeout_probe", "probe_l2_to_smem", "DTYPES"]
 
 DTYPES = {"f32": _lib.PAT_F32, "bf16": _lib.PAT_BF16, "f16": _lib.PAT_F16}
 
@@ -414,6 +414,11 @@ class Server:
         _lib.check(st, "pat_srv_poll")
         return lat
 
+    def set_budget(self, hbm_budget):
+        """pat_srv_set_budget: new HBM budget (bytes); idle subjects beyond it are
+        evicted to their host copies, least recently used first."""
+        _lib.check(self._lib.pat_srv_set_budget(self._h, int(hbm_budget)), "pat_srv_set_budget")
+
     def stats(self):
         st = _lib.PatSrvStats()
         _lib.check(self._lib.pat_srv_stats(self._h, ctypes.byref(st)), "pat_srv_stats")
@@ -474,6 +479,15 @@ def fmm_gpu(speed, dx, origin, sources):
     _lib.check(lib.pat_fmm_gpu(speed.ctypes.data, ctypes.byref(g), src.ctypes.data, src.shape[0],
                                T.ctypes.data), "pat_fmm_gpu")
     return T[0] if one else T
+
+
+def probe_l2_to_smem():
+    """pat_probe_l2_to_smem: aggregate L2 -> shared-memory bulk-copy bandwidth
+    of the current device in GB/s (a roofline of the staged gather)."""
+    lib = _lib.load()
+    v = ctypes.c_double()
+    _lib.check(lib.pat_probe_l2_to_smem(ctypes.byref(v)), "pat_probe_l2_to_smem")
+    return v.value
 
 
 def table_host(speed, dx, origin, sensors, dt, n_samples, mask=None, flags=0):

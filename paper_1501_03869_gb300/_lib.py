@@ -30,7 +30,7 @@ EXPORTS = (
     "pat_plan_info", "pat_plan_destroy", "pat_bp_reconstruct_multi", "pat_bp_autotune",
     "pat_bp_evict", "pat_bp_restore", "pat_srv_create", "pat_srv_register", "pat_srv_submit",
     "pat_srv_poll", "pat_srv_stats", "pat_srv_destroy", "pat_bp_reconstruct_noalloc",
-    "pat_bp_create_constant",
+    "pat_bp_create_constant", "pat_srv_set_budget", "pat_probe_l2_to_smem",
 )
 PAT_FLAG_HOST_MIRROR = 0x100
 PAT_FLAG_STAGED_SINGLE = 0x200
@@ -60,7 +60,7 @@ class PatPlanInfo(ctypes.Structure):
                 ("sensors_per_stage", ctypes.c_int), ("stages", ctypes.c_int),
                 ("smem_budget_kb", ctypes.c_int), ("grid", ctypes.c_int),
                 ("n_units", ctypes.c_int64), ("tuned", ctypes.c_int), ("graph", ctypes.c_int),
-                ("tune_ms", ctypes.c_double)]
+                ("tune_ms", ctypes.c_double), ("n_classes", ctypes.c_int), ("fb_mask", ctypes.c_int)]
 
 
 class PatSrvCfg(ctypes.Structure):
@@ -174,6 +174,10 @@ def load():
         lib.pat_srv_stats.argtypes = [_vp, ctypes.POINTER(PatSrvStats)]
         lib.pat_srv_destroy.restype = _i
         lib.pat_srv_destroy.argtypes = [_vp]
+        lib.pat_srv_set_budget.restype = _i
+        lib.pat_srv_set_budget.argtypes = [_vp, ctypes.c_size_t]
+        lib.pat_probe_l2_to_smem.restype = _i
+        lib.pat_probe_l2_to_smem.argtypes = [ctypes.POINTER(ctypes.c_double)]
         lib.pat_test_wait_timeout.restype = _i
         lib.pat_test_wait_timeout.argtypes = [_u64]
         _lib = lib

@@ -2,7 +2,8 @@
 //
 // Two launches.  The gather kernel is persistent: CTA c takes units (tile,
 // segment of G sensors) c, c + grid, c + 2 grid, ... in tile-major order, and
-// asks L2 for each unit's delay data two units ahead with one bulk prefetch.
+// (constant speed, or signals read from host memory) asks L2 for each unit's
+// delay data two units ahead with one bulk prefetch.
 // Its warps are the (pixel group, sensor phase) pairs of the staged kernel's
 // consumers; a warp reads the delay data (table offsets, or the constant-
 // speed anchors) and the window bases for a chunk of its sensors, then
@@ -51,8 +52,9 @@ struct DirectParams {
   const float* m;
   float* out;
   float* part;  // [n_tiles][n_seg][SW][P] phase sums
-  const int* status;
+  int* status;
   int* host_status;  // the reduction copies *status here when set
+  uint64_t timeout_ns;  // bound of every device-side wait
   int n_zero_runs, n_sensors, n_sensors_pad, n_t_pad, n_tiles, n_seg, G;
 };
 
@@ -113,14 +115,19 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
   const int pg = warp % PW, sp = warp / PW;
   const int px0 = pg * 128 + lane;
   const int64_t n_units = int64_t(p.n_tiles) * p.n_seg;
-  if (DELAYS != 0 && threadIdx.x == 0) {
+  // Delay data is pulled into L2 ahead of use for constant speed, and for a
+  // stored table when the preprocessing reads the signals from host memory
+  // (the host round trip): the table stream then overlaps that slow read
+  // instead of following it.
+  const bool pf = DELAYS != 0 || p.host_status != nullptr;
+  if (pf && threadIdx.x == 0) {
     prefetch_unit<P, DELAYS>(p, blockIdx.x, n_units);
     prefetch_unit<P, DELAYS>(p, int64_t(blockIdx.x) + gridDim.x, n_units);
   }
   const uint32_t* bsrc = static_cast<const uint32_t*>(p.b);
   bool waited = false;
   for (int64_t unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
-    if (DELAYS != 0 && threadIdx.x == 0)
+    if (pf && threadIdx.x == 0)
       prefetch_unit<P, DELAYS>(p, unit + 2 * int64_t(gridDim.x), n_units);
     const int tile = int(unit / p.n_seg);
     const int seg = int(unit - int64_t(tile) * p.n_seg);
@@ -307,20 +314,32 @@ cudaError_t launch_pdl(K kern, unsigned grid, unsigned threads, const DirectPara
   return cudaLaunchKernelEx(&cfg, kern, dp);
 }
 
+constexpr int kMaxDevices = 64;
+
+// Resident CTAs per SM of one kernel, looked up once per device (devices of a
+// process may differ).
+struct PerDevice {
+  int per_sm[kMaxDevices] = {};
+};
+
 template <int P, int SW, int FMT, int DELAYS, int WGT>
 cudaError_t launch_direct_fmt(const DirectParams& dp, int n_sm, cudaStream_t st) {
   auto kern = gather_direct_kernel<P, SW, FMT, DELAYS, WGT>;
   const int threads = 32 * (P / 128) * SW;
-  static int per_sm = 0;  // resident CTAs per SM (per instantiation, looked up once)
-  if (per_sm == 0) {
+  static PerDevice cache;  // resident CTAs per SM, per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (cache.per_sm[dev] == 0) {
     int v = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, 0);
     if (e != cudaSuccess) return e;
-    per_sm = v > 0 ? v : 1;
+    cache.per_sm[dev] = v > 0 ? v : 1;
   }
   const int64_t n_units = int64_t(dp.n_tiles) * dp.n_seg;
-  const unsigned grid = unsigned(std::min<int64_t>(n_units, int64_t(per_sm) * n_sm));
-  cudaError_t e = launch_pdl(kern, grid, unsigned(threads), dp, st);
+  const unsigned grid = unsigned(std::min<int64_t>(n_units, int64_t(cache.per_sm[dev]) * n_sm));
+  e = launch_pdl(kern, grid, unsigned(threads), dp, st);
   if (e != cudaSuccess) return e;
   const int64_t n = int64_t(dp.n_tiles) * P;
   const unsigned rgrid = unsigned(std::min<int64_t>((n + 255) / 256, int64_t(n_sm) * 8));
@@ -348,7 +367,8 @@ size_t direct_part_floats(const GatherConfig& c, int n_tiles, int n_seg) {
 }
 
 cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc& d, int n_sm,
-                                 const int* status, int* host_status, cudaStream_t st) {
+                                 int* status, int* host_status, uint64_t timeout_ns,
+                                 cudaStream_t st) {
   if (d.n_frames != 1 || c.FB != 1 || d.n_fg != 1 || n_sm < 1 || !d.part) return cudaErrorInvalidValue;
   DirectParams dp;
   dp.u = d.u;
@@ -364,6 +384,7 @@ cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc&
   dp.part = d.part;
   dp.status = status;
   dp.host_status = host_status;
+  dp.timeout_ns = timeout_ns;
   dp.n_zero_runs = d.n_zero_runs;
   dp.n_sensors = d.n_sensors;
   dp.n_sensors_pad = d.n_sensors_pad;

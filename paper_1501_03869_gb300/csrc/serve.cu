@@ -50,18 +50,32 @@ struct Subject {
   bool busy = false;
 };
 
+// A result whose host buffer is pageable: the device copies it into the
+// slot's page-locked staging buffer, and the scheduler copies it on to the
+// caller's buffer once the batch is done (outside the server lock).
+struct HostCopy {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
   bool busy = false;
   int subject = -1;
   std::vector<uint64_t> tickets;
+  std::vector<HostCopy> out_copies;
   void* d_sig = nullptr;
   size_t sig_cap = 0;
   float* d_sc = nullptr;
   size_t sc_cap = 0;
   float* d_out = nullptr;
   size_t out_cap = 0;
+  void* h_sig = nullptr;   // page-locked staging of pageable signals and scales
+  size_t h_sig_cap = 0;
+  void* h_out = nullptr;   // page-locked staging of results for pageable buffers
+  size_t h_out_cap = 0;
 };
 
 pat_status grow_dev(void** p, size_t* cap, size_t need) {
@@ -72,6 +86,27 @@ pat_status grow_dev(void** p, size_t* cap, size_t need) {
   if (cudaMalloc(p, need) != cudaSuccess) return fail(PAT_ERR_OOM, "serving staging buffer");
   *cap = need;
   return PAT_OK;
+}
+
+pat_status grow_pinned(void** p, size_t* cap, size_t need) {
+  if (need <= *cap) return PAT_OK;
+  cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMallocHost(p, need) != cudaSuccess) return fail(PAT_ERR_OOM, "serving host staging buffer");
+  *cap = need;
+  return PAT_OK;
+}
+
+// True for page-locked host memory, which copy engines read and write
+// asynchronously (a copy to or from pageable memory can block the host).
+bool page_locked(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
 }
 
 }  // namespace
@@ -123,13 +158,21 @@ void finish(pat_srv_t s, uint64_t t, pat_status st) {
   }
 }
 
-void reap(pat_srv_t s) {
+void reap(pat_srv_t s, std::unique_lock<std::mutex>& lk) {
   bool any = false;
   for (Slot& sl : s->slots) {
     if (!sl.busy) continue;
     cudaError_t e = cudaEventQuery(sl.ev);
     if (e == cudaErrorNotReady) continue;
     pat_status st = e == cudaSuccess ? PAT_OK : cuda_fail(e, "serving batch");
+    if (st == PAT_OK && !sl.out_copies.empty()) {
+      // results of pageable buffers: the slot stays busy (nobody else touches
+      // it or its requests' buffers) while the lock is released for the copies
+      lk.unlock();
+      for (const HostCopy& c : sl.out_copies) std::memcpy(c.dst, c.src, c.bytes);
+      lk.lock();
+    }
+    sl.out_copies.clear();
     if (st == PAT_OK) {
       int flag = 0;
       pat_bp_t h = s->subjects[sl.subject].h;
@@ -187,20 +230,51 @@ pat_status launch_batch(pat_srv_t s, Slot& sl, int k, const std::vector<uint64_t
   const bool lowp = r0.dtype != PAT_F32;
   if (lowp && (st = grow_dev(reinterpret_cast<void**>(&sl.d_sc), &sl.sc_cap, F * h->ns * 4)) != PAT_OK)
     return st;
+  // Inputs: page-locked buffers are copied as they are; pageable ones are first
+  // packed into the slot's page-locked staging buffer (frames, then scales).
+  const size_t sc_row = size_t(h->ns) * 4;
+  size_t staged = 0;
   for (size_t f = 0; f < F; ++f) {
     const Request& r = s->reqs[ts[f]];
-    PAT_CUDA(cudaMemcpyAsync(static_cast<char*>(sl.d_sig) + f * row, r.sig, row,
-                             cudaMemcpyHostToDevice, sl.st));
-    if (lowp)
-      PAT_CUDA(cudaMemcpyAsync(sl.d_sc + f * h->ns, r.scales, size_t(h->ns) * 4,
-                               cudaMemcpyHostToDevice, sl.st));
+    if (!page_locked(r.sig)) staged += row;
+    if (lowp && !page_locked(r.scales)) staged += sc_row;
+  }
+  if (staged && (st = grow_pinned(&sl.h_sig, &sl.h_sig_cap, staged)) != PAT_OK) return st;
+  size_t at = 0;
+  auto copy_in = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (page_locked(src)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, sl.st);
+    char* stage = static_cast<char*>(sl.h_sig) + at;
+    std::memcpy(stage, src, bytes);
+    at += bytes;
+    return cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, sl.st);
+  };
+  for (size_t f = 0; f < F; ++f) {
+    const Request& r = s->reqs[ts[f]];
+    PAT_CUDA(copy_in(static_cast<char*>(sl.d_sig) + f * row, r.sig, row));
+    if (lowp) PAT_CUDA(copy_in(sl.d_sc + f * h->ns, r.scales, sc_row));
   }
   if ((st = reconstruct_locked(h, sl.d_sig, r0.dtype, lowp ? sl.d_sc : nullptr, int(F), sl.d_out,
                                sl.st)) != PAT_OK)
     return st;
-  for (size_t f = 0; f < F; ++f)
-    PAT_CUDA(cudaMemcpyAsync(s->reqs[ts[f]].out, reinterpret_cast<char*>(sl.d_out) + f * out_row,
-                             out_row, cudaMemcpyDeviceToHost, sl.st));
+  // Results: straight into page-locked buffers, else into the staging buffer
+  // (copied on to the caller's buffer when the batch is reaped).
+  size_t n_pageable = 0;
+  for (size_t f = 0; f < F; ++f) n_pageable += page_locked(s->reqs[ts[f]].out) ? 0 : 1;
+  if (n_pageable && (st = grow_pinned(&sl.h_out, &sl.h_out_cap, n_pageable * out_row)) != PAT_OK)
+    return st;
+  sl.out_copies.clear();
+  size_t n_staged = 0;
+  for (size_t f = 0; f < F; ++f) {
+    float* dst = s->reqs[ts[f]].out;
+    const char* src = reinterpret_cast<const char*>(sl.d_out) + f * out_row;
+    if (page_locked(dst)) {
+      PAT_CUDA(cudaMemcpyAsync(dst, src, out_row, cudaMemcpyDeviceToHost, sl.st));
+    } else {
+      char* stage = static_cast<char*>(sl.h_out) + n_staged++ * out_row;
+      PAT_CUDA(cudaMemcpyAsync(stage, src, out_row, cudaMemcpyDeviceToHost, sl.st));
+      sl.out_copies.push_back(HostCopy{dst, stage, out_row});
+    }
+  }
   PAT_CUDA(cudaEventRecord(sl.ev, sl.st));
   return PAT_OK;
 }
@@ -266,7 +340,7 @@ void scheduler_main(pat_srv_t s) {
       std::this_thread::sleep_for(std::chrono::microseconds(s->cfg.stall_us));
       lk.lock();
     }
-    reap(s);
+    reap(s, lk);
     schedule(s);
     bool busy = false;
     for (const Slot& sl : s->slots) busy = busy || sl.busy;
@@ -398,6 +472,29 @@ extern "C" pat_status pat_srv_stats(pat_srv_t s, pat_srv_stats_t* out) {
   return PAT_OK;
 }
 
+extern "C" pat_status pat_srv_set_budget(pat_srv_t s, size_t hbm_budget) {
+  if (!s) return fail(PAT_ERR_INVALID, "NULL server");
+  if (hbm_budget == 0) return fail(PAT_ERR_INVALID, "hbm_budget must be > 0");
+  std::lock_guard<std::mutex> lk(s->mu);
+  cudaSetDevice(s->device);
+  s->budget = hbm_budget;
+  // idle subjects leave, least recently used first, until the rest fit; busy
+  // ones stay until their batches are done (admissions then respect the budget)
+  while (resident_total(s) > s->budget) {
+    int victim = -1;
+    for (int i = 0; i < int(s->subjects.size()); ++i) {
+      const Subject& c = s->subjects[i];
+      if (c.busy || c.h->evicted) continue;
+      if (victim < 0 || c.last_use < s->subjects[victim].last_use) victim = i;
+    }
+    if (victim < 0) break;
+    pat_status e = evict_locked(s->subjects[victim].h);
+    if (e != PAT_OK) return e;
+    ++s->evictions;
+  }
+  return PAT_OK;
+}
+
 extern "C" pat_status pat_srv_destroy(pat_srv_t s) {
   if (!s) return PAT_OK;
   {
@@ -412,6 +509,8 @@ extern "C" pat_status pat_srv_destroy(pat_srv_t s) {
     cudaFree(sl.d_sig);
     cudaFree(sl.d_sc);
     cudaFree(sl.d_out);
+    cudaFreeHost(sl.h_sig);
+    cudaFreeHost(sl.h_out);
     if (sl.ev) cudaEventDestroy(sl.ev);
     if (sl.st) cudaStreamDestroy(sl.st);
   }
