@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-constant", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--serving-requests", type=int, default=200)
     return ap.parse_args()
 
 
@@ -70,6 +70,14 @@ def max_over_ranks(value, world, dist=None, device=None):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def peaks_sm_mhz():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return float(json.load(fh).get("sm_max_mhz", 2070.0))
+    return 2070.0
 
 
 def peaks():
@@ -213,6 +221,100 @@ def oracle_cpu_rate_all_cores(w, n_sensors, seconds):
     return sum(u / t for u, t in res), len(jobs)
 
 
+def _oracle_table_chunk(args):
+    speed, dx, origin, sensors, pix = args
+    import oracle
+    return oracle.travel_table(speed, dx, origin, sensors, pix)
+
+
+def oracle_tables_all_cores(speed, dx, origin, sensors, pix):
+    """The oracle's fast-marching table T[ns, npix], sensors split over one
+    spawn-started process per host core; returns (T, seconds, workers)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    n_w = max(1, os.cpu_count() or 1)
+    sensors = np.asarray(sensors, dtype=np.float64)
+    bounds = np.linspace(0, sensors.shape[0], min(4 * n_w, sensors.shape[0]) + 1).astype(int)
+    jobs = [(np.asarray(speed, dtype=np.float64), dx, np.asarray(origin), sensors[a:b], np.asarray(pix))
+            for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=n_w, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_oracle_table_chunk, jobs))
+    return np.concatenate(parts, axis=0), time.perf_counter() - t0, n_w
+
+
+def accuracy(got, ref, p0max):
+    """rel-L2 and max-abs / max|p0| of one image against the oracle's."""
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    return {"rel_l2": float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)),
+            "max_abs_over_p0": float(np.abs(got - ref).max() / p0max)}
+
+
+def oracle_leg(w, checks):
+    """Host leg after the timed region: the oracle's own table build (one core
+    and all cores) and every form's accuracy against the oracle on the same
+    seeded inputs (FP32 gate rel-L2 1e-5, max-abs 1e-4 max|p0|; 16-bit gate
+    rel-L2 5e-3 against the oracle on the original FP32 signals)."""
+    import oracle
+    from paper_1501_03869_gb300 import synth
+    pix = np.flatnonzero(w.mask.ravel())
+    out = {}
+    n1 = 16
+    t0 = time.perf_counter()
+    oracle.travel_table(w.speed, w.dx, w.origin, w.sensors[:n1], pix)
+    one = (time.perf_counter() - t0) / n1
+    T, t_all, n_w = oracle_tables_all_cores(w.speed, w.dx, w.origin, w.sensors, pix)
+    out["oracle_table_build_c2"] = {
+        "sensors": int(w.n_sensors), "one_core_s_per_sensor": one,
+        "one_core_s_extrapolated": one * w.n_sensors, "all_cores_s": t_all, "cores": n_w,
+        "sample": f"one core: the first {n1} sensors' fast marching, timed and scaled to "
+                  f"{w.n_sensors}; all cores: every sensor, one spawn-started process per core"}
+    acc = {}
+    p0 = float(np.abs(w.p0).max())
+    ref1 = oracle.bp(T, w.signals[0].astype(np.float64), w.dt)
+    if "single_f32" in checks:
+        acc["single_f32"] = accuracy(checks["single_f32"].ravel()[pix], ref1, p0)
+    for name in ("batched_f32", "batched_bf16"):
+        if name not in checks:
+            continue
+        sigF, imgs, frames = checks[name]
+        worst = None
+        for f in frames:
+            ref = oracle.bp(T, sigF[f].astype(np.float64), w.dt)
+            a = accuracy(imgs[f].ravel()[pix], ref, p0 * float(np.abs(sigF[f]).max() /
+                                                               np.abs(w.signals[0]).max()))
+            if worst is None or a["rel_l2"] > worst["rel_l2"]:
+                worst = a
+        worst["frames_checked"] = list(frames)
+        acc[name] = worst
+    if "constant_f32" in checks:
+        c0, img = checks["constant_f32"]
+        Tc = oracle.constant_table(w.speed.shape, w.dx, w.origin, w.sensors, pix, c0)
+        acc["constant_speed_f32"] = accuracy(img.ravel()[pix],
+                                             oracle.bp(Tc, w.signals[0].astype(np.float64), w.dt), p0)
+    if "c1" in checks:
+        w1, img = checks["c1"]
+        pix1 = np.flatnonzero(w1.mask.ravel())
+        T1 = oracle.travel_table(w1.speed, w1.dx, w1.origin, w1.sensors, pix1)
+        acc["latency_c1_f32"] = accuracy(img.ravel()[pix1],
+                                         oracle.bp(T1, w1.signals[0].astype(np.float64), w1.dt),
+                                         float(np.abs(w1.p0).max()))
+    for key, (wi, img) in checks.get("c4", {}).items():
+        pixi = np.flatnonzero(wi.mask.ravel())
+        Ti, _, _ = oracle_tables_all_cores(wi.speed, wi.dx, wi.origin, wi.sensors, pixi)
+        worst = None
+        for f in range(wi.n_frames):
+            a = accuracy(img[f].ravel()[pixi], oracle.bp(Ti, wi.signals[f].astype(np.float64), wi.dt),
+                         float(np.abs(wi.p0).max()))
+            if worst is None or a["rel_l2"] > worst["rel_l2"]:
+                worst = a
+        worst["frames"] = int(wi.n_frames)
+        acc[key] = worst
+    out["accuracy_vs_oracle"] = acc
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -249,7 +351,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def multi_form(args, flush, stream):
+def multi_form(args, flush, stream, checks):
     """Uneven instances in one persistent launch: the 32-instance workload
     (grids 96^2-384^2, 128-1024 sensors, 1024-4096 samples, 1-16 frames),
     autotuned, replayed as a CUDA graph; L2 flushed before every execution."""
@@ -265,7 +367,7 @@ def multi_form(args, flush, stream):
     Ev = torch.cuda.Event
     recs = []
     for i in range(max(5, min(args.steps // 100, 40)) + 3):
-        flush.zero_()
+        flush()
         e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
         e0.record(stream)
         plan.execute(sig, outs, stream=stream)
@@ -273,61 +375,155 @@ def multi_form(args, flush, stream):
         recs.append((e0, e1))
     plan.sync(stream)
     ms = statistics.mean(a.elapsed_time(b) for a, b in recs[3:])
+    cost = sorted((w.n_frames * w.n_sensors * w.n_pix, i) for i, w in enumerate(ws))
+    checks["c4"] = {f"multi_c4_inst{i}": (ws[i], outs[i].cpu().numpy())
+                    for i in (cost[0][1], cost[-1][1])}
     frames = sum(w.n_frames for w in ws)
     upd = sum(w.n_frames * w.n_sensors * w.n_pix for w in ws)
     info = plan.info
+    # HBM bytes one execution must move: every instance's table once per
+    # frame group (frames per unit FB_i), its signals, and its image
+    hbm = 0.0
+    for bp, w in zip(bps, ws):
+        fb = min(8, 1 << (w.n_frames.bit_length() - 1))
+        passes = -(-w.n_frames // fb)
+        hbm += passes * bp.info["table_bytes"] + 4.0 * w.n_frames * w.n_sensors * w.nt \
+            + 4.0 * w.n_frames * w.n_pix
+    hbm_peak, kind = peaks()
     plan.close()
     for bp in bps:
         bp.close()
-    return {"workload": "32 uneven instances, one persistent launch, CUDA graph", "frames": frames,
-            "ms_per_execution": ms, "frames_per_s": frames / (ms / 1e3),
+    return {"workload": "32 uneven instances (grids 96^2-384^2, 128-1024 sensors, 1024-4096 samples, "
+                        "1-16 frames), instances grouped by frames per unit, CUDA graph",
+            "frames": frames, "ms_per_execution": ms, "frames_per_s": frames / (ms / 1e3),
             "value": upd / (ms / 1e3) / 1e9, "unit": UNIT, "launch_shape": info,
-            "gpu_launches_per_execution": 2}
+            "gpu_launches_per_execution": 2 * info["n_classes"],
+            "roofline": {"bound": "hbm", "algorithmic_bytes": hbm,
+                         "achieved": hbm / (ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hbm / (ms / 1e3) / 1e9 / hbm_peak, "peak_source": kind,
+                         "note": "tables once per frame group, signals and images; the HBM floor, "
+                                 "not the binding resource (shared-memory window traffic is)"}}
 
 
 def serving_form(args):
-    """Request loop over several 3-D subjects (hemisphere of sensors around a
-    spherical-shell skull, BF16 signals of 2048 samples): Poisson arrivals at
-    several rates, frames/s and p50/p99 submit-to-done latency."""
-    import torch  # noqa: F401  (CUDA context)
-    from paper_1501_03869_gb300 import Server, synth
-    shape, n_s, n_sub = (48, 80, 80), 256, 4
-    subs = [synth.config5_subject(k, n_frames=4, n_sensors=n_s, shape=shape, dx=0.5e-3)
-            for k in range(n_sub)]
+    """The 3-D serving workload at full size: 8 subjects (160x160x96 voxels at
+    0.25 mm, all 2 457 600 reconstructed, 1024 sensors on a hemisphere,
+    spherical-shell skull 2200-3000 m/s), tables solved on the GPU, BF16
+    signals of 2048 samples submitted from page-locked buffers, results into
+    page-locked buffers.  Poisson arrivals (subjects uniform) at 50, 100, 200
+    and 400 frames/s and a saturating burst under a 120 GB HBM budget, then a
+    40 GB budget that holds three subjects, so admissions evict the least
+    recently used table and reload it from its host copy inside the latency."""
+    import torch
+    from paper_1501_03869_gb300 import Server, _lib, synth
+    n_sub = 8
+    subs = [synth.config5_subject(k, n_frames=2) for k in range(n_sub)]
     srv = Server(hbm_budget=120 << 30, n_streams=4, max_batch_frames=16)
-    ids = [srv.register(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask) for w in subs]
-    q = [synth.quantise(w.signals, "bf16") for w in subs]
+    t0 = time.perf_counter()
+    ids = [srv.register(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+                        flags=_lib.PAT_FLAG_GPU_TABLE) for w in subs]
+    reg_s = (time.perf_counter() - t0) / n_sub
+    inp = []
+    for w in subs:
+        codes, sc, _ = synth.quantise(w.signals, "bf16")
+        c = torch.empty(codes.shape, dtype=torch.int16, pin_memory=True).numpy().view(np.uint16)
+        c[:] = codes
+        scl = torch.empty(sc.shape, dtype=torch.float32, pin_memory=True).numpy()
+        scl[:] = sc
+        inp.append((c, scl))
+    ring = [torch.empty(subs[0].speed.shape, dtype=torch.float32, pin_memory=True).numpy()
+            for _ in range(64)]
+    ring_t = [None] * len(ring)
     rng = np.random.default_rng(5)
-    out = {"workload": f"{n_sub} 3-D subjects {shape[::-1]} at 0.5 mm, {n_s} sensors on a hemisphere, "
-                       "BF16 signals of 2048 samples, HBM budget 120 GB", "rates": []}
-    for rate in (200.0, 800.0, 3200.0):
-        n = args.serving_requests
-        gaps = rng.exponential(1.0 / rate, n)
-        pending = []
-        t0 = time.perf_counter()
-        t_next = t0
+
+    def run(rate, n):
+        st0 = srv.stats()
+        lat = []
+        t_start = time.perf_counter()
+        t_next = t_start
         for i in range(n):
-            t_next += gaps[i]
-            while time.perf_counter() < t_next:
-                pass
-            k = int(rng.integers(n_sub))
-            f = int(rng.integers(subs[k].n_frames))
-            codes, sc, _ = q[k]
-            o = np.empty(subs[k].speed.shape, np.float32)
-            pending.append(srv.submit(ids[k], codes[f], o, dtype="bf16", scales=sc[f]))
-        lat = [srv.wait(t) for t in pending]
-        el = time.perf_counter() - t0
-        out["rates"].append({"offered_fps": rate, "requests": n, "frames_per_s": n / el,
-                             "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                             "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+            if rate:
+                t_next += rng.exponential(1.0 / rate)
+                while time.perf_counter() < t_next:
+                    pass
+            j = i % len(ring)
+            if ring_t[j] is not None:  # the ring slot's earlier request must be done
+                lat.append(srv.wait(ring_t[j], timeout_s=300.0))
+            k, f = int(rng.integers(n_sub)), int(rng.integers(2))
+            ring_t[j] = srv.submit(ids[k], inp[k][0][f], ring[j], dtype="bf16", scales=inp[k][1][f])
+        for j in range(len(ring)):
+            if ring_t[j] is not None:
+                lat.append(srv.wait(ring_t[j], timeout_s=300.0))
+                ring_t[j] = None
+        el = time.perf_counter() - t_start
+        st1 = srv.stats()
+        nb = st1["batches"] - st0["batches"]
+        nf = st1["mean_batch_frames"] * st1["batches"] - st0["mean_batch_frames"] * st0["batches"]
+        return {"offered_fps": rate if rate else "burst", "requests": n, "frames_per_s": n / el,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_batch_frames": nf / max(nb, 1), "batches": nb,
+                "evictions": st1["evictions"] - st0["evictions"],
+                "uploads": st1["uploads"] - st0["uploads"]}
+
+    n = args.serving_requests
+    run(None, 16)  # warm-up: every subject's working buffers allocated
+    out = {"workload": "8 subjects 160x160x96 at 0.25 mm (2 457 600 voxels each), 1024 sensors on "
+                       "a hemisphere, BF16 signals of 2048 samples, page-locked host buffers",
+           "updates_per_frame": int(subs[0].n_pix) * 1024,
+           "register_s_per_subject": reg_s, "budget_gb": 120, "rates": []}
+    for rate in (50.0, 100.0, 200.0, 400.0):
+        out["rates"].append(run(rate, n))
+    out["rates"].append(run(None, 4 * n))
     st = srv.stats()
-    out["mean_batch_frames"] = st["mean_batch_frames"]
-    out["batches"] = st["batches"]
+    out["resident_gb_at_120"] = st["resident_bytes"] / 2**30
+    srv.set_budget(40 << 30)
+    out["evict_40gb"] = run(50.0, max(n // 4, 20))
+    out["evict_40gb"]["resident_gb"] = srv.stats()["resident_bytes"] / 2**30
     srv.close()
     return out
 
 
-def constant_form(args, w, flush, stream):
+def serving_batching_form(args, w):
+    """Continuous batching against no batching on the paper-shaped frame: a
+    burst of requests (64 distinct FP32 frames, page-locked buffers) through a
+    server that batches up to 16 frames of a subject and through one that runs
+    every frame alone; frames/s of both and whether every result has the same
+    bits in both."""
+    import torch
+    from paper_1501_03869_gb300 import Server
+    F = 64
+    rng = np.random.default_rng(11)
+    frames = torch.empty((F,) + w.signals.shape[1:], dtype=torch.float32, pin_memory=True).numpy()
+    frames[:] = (w.signals[0][None] * rng.uniform(0.5, 1.5, (F, 1, 1))).astype(np.float32)
+    res, outs = {}, {}
+    for name, mb in (("batched", 16), ("unbatched", 1)):
+        srv = Server(hbm_budget=8 << 30, n_streams=4, max_batch_frames=mb)
+        sid = srv.register(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask)
+        out = torch.empty((F,) + w.speed.shape, dtype=torch.float32, pin_memory=True).numpy()
+        for f in range(8):  # warm-up: working buffers and streams
+            srv.wait(srv.submit(sid, frames[f], out[f]))
+        reps = max(2, args.serving_requests // F)
+        t0 = time.perf_counter()
+        lat = []
+        for _ in range(reps):
+            ts = [srv.submit(sid, frames[f], out[f]) for f in range(F)]
+            lat += [srv.wait(t) for t in ts]
+        el = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        res[name] = {"frames_per_s": reps * F / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                     "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                     "mean_batch_frames": st["mean_batch_frames"], "max_batch_frames": mb}
+        outs[name] = out
+    res["gain"] = res["batched"]["frames_per_s"] / res["unbatched"]["frames_per_s"]
+    res["same_bits"] = bool(np.array_equal(outs["batched"], outs["unbatched"]))
+    res["workload"] = ("paper-shaped frame, bursts of 64 distinct FP32 frames from page-locked "
+                       "buffers, results into page-locked buffers")
+    return res
+
+
+def constant_form(args, w, flush, stream, checks):
     """The conventional back projection of the same frame (Sec. III's
     comparison method, 1560 m/s): delays computed in the gather kernel, no
     table stream.  Single frame as a replayed CUDA graph, and 64 frames."""
@@ -369,6 +565,7 @@ def constant_form(args, w, flush, stream):
 
     rr = time_steps(step, max(50, min(args.steps, 1000)), args.warmup, stream, flush)
     ms = statistics.mean(a.elapsed_time(b) for a, b in rr)
+    checks["constant_f32"] = (C_CONSTANT_BP, out.cpu().numpy()[0])
     form = {"c0": C_CONSTANT_BP, "ms_per_step": ms, "frames_per_s": 1e3 / ms,
             "value": updates / (ms / 1e3) / 1e9, "unit": UNIT,
             "path_us": statistics.mean(a.elapsed_time(b) for a, b in kr) * 1e3,
@@ -396,17 +593,138 @@ def constant_form(args, w, flush, stream):
     return form
 
 
+def batched_roofline(w, tile_flags, F, FB, shared_read_bytes, gather_ms, sm_mhz, n_sm, l2_smem_gbs):
+    """Roofline of the staged gather on F frames: the larger of the
+    shared-memory time (gather reads plus the bulk copies' writes, 128 B per
+    clock per SM) and the L2 -> shared stream time (window and table-block
+    copies against the measured bulk-copy bandwidth), against the measured
+    gather time.  Window rows per (tile, sensor) are the library's: from the
+    first integer sample of the tile's arrivals to two past the last, in
+    multiples of 8."""
+    from paper_1501_03869_gb300 import table_host
+    info, u, base, slot = table_host(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+                                     flags=tile_flags)
+    P, nt_, ns = info["tile_pix"], info["n_tiles"], w.n_sensors
+    uu = np.where(u < 1e29, u, np.nan).reshape(nt_, ns, P)
+    mx = np.nan_to_num(np.nanmax(uu, axis=2), nan=0.0)
+    rows = np.ceil((np.floor(mx) + 3) / 8) * 8
+    n_fg = -(-F // FB)
+    n_pix = int(info["n_pix"])
+    win = float(rows.sum()) * FB * 4 * n_fg                  # window copies
+    tab = float(nt_ * ns * P * 4) * n_fg                     # table blocks
+    upd = F * ns * n_pix
+    smem_bytes = shared_read_bytes * upd + win + tab
+    xbar_bytes = win + tab
+    smem_peak = 128.0 * n_sm * sm_mhz * 1e6 / 1e9
+    t_smem = smem_bytes / (smem_peak * 1e9)
+    t_xbar = xbar_bytes / (l2_smem_gbs * 1e9)
+    bound = "smem" if t_smem >= t_xbar else "l2_to_smem"
+    t = max(t_smem, t_xbar)
+    return {"bound": bound, "frac": t / (gather_ms / 1e3), "gather_ms": gather_ms,
+            "smem_bytes": smem_bytes, "smem_peak_GBps": smem_peak,
+            "smem_achieved_GBps": smem_bytes / (gather_ms / 1e3) / 1e9,
+            "l2_to_smem_bytes": xbar_bytes, "l2_to_smem_peak_GBps": l2_smem_gbs,
+            "l2_to_smem_achieved_GBps": xbar_bytes / (gather_ms / 1e3) / 1e9,
+            "shared_read_bytes_per_update": shared_read_bytes,
+            "window_rows_per_pixel_sensor": float(rows.sum()) / (ns * n_pix),
+            "frames_per_unit": FB, "peak_source": "smem: 128 B/clk/SM x SMs x max SM clock; "
+                                                  "l2_to_smem: bulk-copy bandwidth measured in this "
+                                                  "run (pat_probe_l2_to_smem)"}
+
+
+def time_steps_warm(fn, steps, warmup):
+    """Per-step spans of fn() with nothing between the steps (warm L2)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    recs = [fn() for _ in range(steps)]
+    torch.cuda.synchronize()
+    return recs
+
+
+def c1_form(args, flush, stream, checks):
+    """Latency of the small single-frame workload (128x128 grid, 64 sensors,
+    1024 samples, 6 092 pixels): the user call replayed as a CUDA graph, L2
+    flushed (cold) and not (warm), by events; and through the host round trip
+    (page-locked buffers, wall clock)."""
+    import torch
+    from paper_1501_03869_gb300 import BP, synth
+    Ev = torch.cuda.Event
+    w1 = synth.config1(n_frames=1)
+    bp1 = BP(w1.speed, w1.dx, w1.origin, w1.sensors, w1.dt, w1.nt, mask=w1.mask)
+    sig = torch.from_numpy(w1.signals).cuda()
+    out = torch.empty(bp1.out_shape(1), device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        bp1.reconstruct(sig, out=out, stream=side)
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bp1.reconstruct(sig, out=out, stream=torch.cuda.current_stream())
+
+    def step():
+        e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        return e0, e1
+
+    n = max(50, min(args.steps, 1000))
+    cold = [a.elapsed_time(b) for a, b in time_steps(step, n, args.warmup, stream, flush)]
+    warm = [a.elapsed_time(b) for a, b in time_steps_warm(step, n, args.warmup)]
+    checks["c1"] = (w1, out.cpu().numpy()[0])
+    pin_sig = torch.empty(w1.signals.shape, dtype=torch.float32, pin_memory=True).numpy()
+    pin_sig[:] = w1.signals
+    pin_out = torch.empty(bp1.out_shape(1), dtype=torch.float32, pin_memory=True).numpy()
+    for _ in range(args.warmup):
+        bp1.reconstruct_host(pin_sig, out=pin_out)
+    host = []
+    for _ in range(min(n, 300)):
+        t0 = time.perf_counter()
+        bp1.reconstruct_host(pin_sig, out=pin_out)
+        host.append(time.perf_counter() - t0)
+    bp1.close()
+    upd = int(w1.n_pix) * w1.n_sensors
+    return {"workload": "128x128 at 0.2 mm, 64 sensors, 1024 FP32 samples, 6092-pixel mask",
+            "device_cold_p50_us": float(np.percentile(cold, 50) * 1e3),
+            "device_cold_p99_us": float(np.percentile(cold, 99) * 1e3),
+            "device_warm_p50_us": float(np.percentile(warm, 50) * 1e3),
+            "host_round_trip_p50_us": float(np.percentile(host, 50) * 1e6),
+            "host_round_trip_p99_us": float(np.percentile(host, 99) * 1e6),
+            "value_cold": upd / (statistics.mean(cold) / 1e3) / 1e9, "unit": UNIT}
+
+
+class L2Flush:
+    """Empties the L2 (129 MB) before a timed step: a 512 MB write, then a
+    256 MB read of another buffer.  The read evicts the write's dirty lines
+    (writing them back) before the step starts, so the step's DRAM traffic is
+    its own, not the flush's write-back, while nothing the step reads is left
+    in L2."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.r = torch.zeros(L2_FLUSH_BYTES // 8, dtype=torch.float32, device=dev)
+        self.sink = None
+
+    def __call__(self):
+        self.w.zero_()
+        self.sink = self.r.sum()
+
+
 def time_steps(fn, steps, warmup, stream, flush):
     """Per-step device times (ms) of fn(); L2 flushed before every step, events
     on `stream`.  fn returns a list of (name, start_evt, end_evt) spans."""
     import torch
     for _ in range(warmup):
-        flush.zero_()
+        flush()
         fn()
     torch.cuda.synchronize()
     recs = []
     for _ in range(steps):
-        flush.zero_()
+        flush()
         recs.append(fn())
     torch.cuda.synchronize()
     return recs
@@ -435,7 +753,7 @@ def main():
     updates = n_pix * ns
     sig = torch.from_numpy(w.signals).to(dev)
     out = torch.empty(bp.out_shape(1), device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     bp.reserve(max(args.batch_frames, 1))
     # (one frame takes the unstaged gather, which has no launch shape to tune)
     Ev = torch.cuda.Event
@@ -484,7 +802,7 @@ def main():
 
     # ---------------------------------------------------- timed single frame --
     for _ in range(args.warmup):
-        flush.zero_()
+        flush()
         step()
     torch.cuda.synchronize()
     if world > 1:
@@ -496,7 +814,7 @@ def main():
         wall0 = time.perf_counter()
         recs = []
         for _ in range(args.steps):
-            flush.zero_()
+            flush()
             recs.append(step())
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
@@ -532,7 +850,7 @@ def main():
         bp.reconstruct_host(sig_np, out=out_np)
     e2e_t = []
     for _ in range(min(args.steps, 500)):
-        flush.zero_()
+        flush()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         bp.reconstruct_host(sig_np, out=out_np)
@@ -547,9 +865,21 @@ def main():
 
     # --------------------------------------------------------------- forms --
     forms = {}
+    checks = {"single_f32": out.cpu().numpy()[0]}
+    # warm L2: the same replayed step without the flush (table and integrand
+    # stay in the 129 MB L2 between steps)
+    warm = time_steps_warm(step, max(50, min(args.steps, 1000)), args.warmup)
+    warm_ms = statistics.mean(a.elapsed_time(b) for a, b in warm)
+    forms["single_f32_warm_l2"] = {"ms_per_step": warm_ms, "value": updates / (warm_ms / 1e3) / 1e9,
+                                   "unit": UNIT, "frames_per_s": 1e3 / warm_ms}
+    if not args.no_forms:
+        forms["latency_c1"] = c1_form(args, flush, stream, checks)
     if not args.no_forms and args.batch_frames > 1:
         F = args.batch_frames
         from paper_1501_03869_gb300 import _lib
+        from paper_1501_03869_gb300 import probe_l2_to_smem
+        l2s = probe_l2_to_smem()
+        forms["l2_to_smem_bulk_GBps"] = l2s
         bpb = BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
                  flags=_lib.PAT_FLAG_TILE_256)
         rng = np.random.default_rng(7)
@@ -570,8 +900,28 @@ def main():
             n_rep = max(3, args.steps // 5)
             rr = time_steps(fstep, n_rep, 2, stream, flush)
             ms = statistics.mean(a.elapsed_time(b) for a, b in rr)
+
+            def gstep(s=s, scl=scl):
+                e0, e1, e2 = Ev(enable_timing=True), Ev(enable_timing=True), Ev(enable_timing=True)
+                e0.record(stream)
+                bpb.preprocess(s, scales=scl, stream=stream)
+                e1.record(stream)
+                bpb.gather(F, outF, stream=stream)
+                e2.record(stream)
+                return e0, e1, e2
+            rg = time_steps(gstep, n_rep, 2, stream, flush)
+            g_ms = statistics.mean(b.elapsed_time(c) for a, b, c in rg)
+            FB = min(8, 1 << (F.bit_length() - 1))
             forms[name] = {"frames": F, "ms_per_batch": ms, "frames_per_s": F / (ms / 1e3),
-                           "value": F * updates / (ms / 1e3) / 1e9, "unit": UNIT, "tile_pix": 256}
+                           "value": F * updates / (ms / 1e3) / 1e9, "unit": UNIT, "tile_pix": 256,
+                           "gather_ms": g_ms,
+                           "roofline": batched_roofline(
+                               w, _lib.PAT_FLAG_TILE_256, F, FB, 8.0 if scl is None else 4.0, g_ms,
+                               peaks_sm_mhz(), torch.cuda.get_device_properties(dev).multi_processor_count,
+                               l2s)}
+            picks = sorted({0, F // 3, (2 * F) // 3, F - 1})
+            imgs = outF.cpu().numpy()
+            checks[name] = (sigF.cpu().numpy(), {f: imgs[f] for f in picks}, picks)
         bpb.sync()
         bpb.close()
 
@@ -587,11 +937,12 @@ def main():
                                    "host_threads": os.cpu_count(),
                                    "gpu_solver_s": gpu_s}
     if not args.no_constant:
-        forms["constant_speed_c2"] = constant_form(args, w, flush, stream)
+        forms["constant_speed_c2"] = constant_form(args, w, flush, stream, checks)
     if not args.no_multi and world == 1:
-        forms["multi_instance_c4"] = multi_form(args, flush, stream)
+        forms["multi_instance_c4"] = multi_form(args, flush, stream, checks)
     if not args.no_serving and world == 1:
-        forms["serving_3d"] = serving_form(args)
+        forms["serving_batching_c2"] = serving_batching_form(args, w)
+        forms["serving_c5_full"] = serving_form(args)
 
     # -------------------------------------------------------- cpu baseline --
     cpu = None
@@ -606,6 +957,7 @@ def main():
             forms["cpu_oracle_all_cores"] = {
                 "value": rate_all / 1e9, "unit": UNIT, "cores": n_w, "kind": "oracle",
                 "sample": f"the same back projection over pixel chunks, one process per host core"}
+            forms.update(oracle_leg(w, checks))
 
     if rank == 0:
         line = {
@@ -617,7 +969,8 @@ def main():
             "config": {"workload": WORKLOAD, "global_batch": world, "n_sensors": ns,
                        "n_pix": n_pix, "n_samples": nt, "tile_pix": info["tile_pix"],
                        "split": info["split"], "parallelism": f"replicas x{world}",
-                       "l2": "flushed before every step (512 MB write)"},
+                       "l2": "flushed before every step: 512 MB write, then a 256 MB read of "
+                             "another buffer (no dirty flush lines left to write back in the step)"},
             "gpu_launches": 3 * args.steps,
             "step": "CUDA graph of pat_bp_reconstruct (preprocessing + gather + segment reduction), "
                     "replayed",

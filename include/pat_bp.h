@@ -285,7 +285,7 @@ pat_status pat_table_host(const float* speed_host, const pat_grid* grid, const d
  * Many instances in persistent launches (uneven grids, sensor counts, sample
  * counts and frame counts).  A plan fixes the handles and their frame counts
  * and groups the instances by frames per unit FB (the largest power of two up
- * to 16 not above an instance's frame count: FB frames share each pass over a
+ * to 8 not above an instance's frame count: FB frames share each pass over a
  * table tile).  Each execution runs one preprocessing launch per group, then
  * one persistent gather launch per group (the first programmatically
  * dependent on the preprocessing), optionally replayed as a CUDA graph.  The

@@ -77,89 +77,6 @@ __device__ __forceinline__ void solid_angle_weights(float (&ww)[4], const float4
   for (int x = 0; x < 4; ++x) ww[x] = solid_angle_weight(pq[x], E, N);
 }
 
-// Constant-speed delay (window offset) of one pixel for a sensor's anchor
-// (A, B) -- the arithmetic of gather_sensor_const below, for one pixel.
-__device__ __forceinline__ float const_delay(const float4 pq, float4 A, float4 B) {
-  if (B.w == 0.0f) {
-    const float num = fmaf(pq.x, A.x, fmaf(pq.y, A.y, fmaf(pq.z, A.z, pq.w)));
-    const float s = num + B.z;
-    const float y = rsqrtf(s);
-    const float da = s * y - A.w;
-    const float r = fmaf(-da, da, fmaf(-2.0f * A.w, da, num));
-    const float v = fmaf(r, 0.5f * y, da) + B.x;
-    return v > B.y ? kFarOffset : fmaxf(v, 0.0f);
-  }
-  const float d0 = fmaf(0.5f, pq.x, A.x), d1 = fmaf(0.5f, pq.y, A.y), d2 = fmaf(0.5f, pq.z, A.z);
-  const float s = fmaxf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), 1.0e-30f);
-  const float v = (s * rsqrtf(s) - A.w) + B.x;
-  return v > B.y ? kFarOffset : fmaxf(v, 0.0f);
-}
-
-// Units of 16 frames ("wide" units).  A row of the integrand holds 16 frames
-// (64 bytes: four 16-byte chunks of 4 frames); lane (g, c) = (lane / 4,
-// lane % 4) of a consumer warp owns frames 4c .. 4c + 3 of the warp's pixels
-// g, g + 8, ..., g + 56.  So the 8 lanes of a 16-byte shared-memory load phase
-// read whole rows of 2 pixels, and the chunks of row r are stored rotated,
-// physical chunk = c ^ ((r / 2) mod 4), which puts two rows that share their
-// bank half (r = r' mod 2) on different banks unless r = r' mod 8.  Window
-// copies start at rows that are multiples of 8 in global and shared memory,
-// so the rotation of a row is the same in both.
-__device__ __forceinline__ unsigned wide_chunk(unsigned r, int c) { return unsigned(c) ^ ((r >> 1) & 3u); }
-
-// One sensor of a stage for a wide unit: offsets uu of the lane's 8 pixels
-// (sample rows from the sensor's window start), multipliers of the lane's 4
-// frames; acc[j][f] += m_f * w_j * lerp.  Same arithmetic per (pixel, frame)
-// as lerp_accumulate.
-template <int FMT, int WGT>
-__device__ __forceinline__ void lerp_accumulate_wide(float (&acc)[8][4], const float (&uu)[8],
-                                                     const float (&ww)[8], const uint32_t* sm, int off,
-                                                     const uint32_t* sw, int Wst, int c) {
-  const unsigned lim = unsigned(Wst - off);
-  float mm[4];
-  {
-    const uint4 q = *reinterpret_cast<const uint4*>(sm + 4 * c);
-    mm[0] = __uint_as_float(q.x);
-    mm[1] = __uint_as_float(q.y);
-    mm[2] = __uint_as_float(q.z);
-    mm[3] = __uint_as_float(q.w);
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const unsigned i = min(unsigned(__float2int_rz(uu[j])), lim);
-    const float ph = uu[j] - float(i);
-    const unsigned r = i + unsigned(off);
-    const uint4 q0 = *reinterpret_cast<const uint4*>(sw + r * 16u + (wide_chunk(r, c) << 2));
-    const uint32_t w0[4] = {q0.x, q0.y, q0.z, q0.w};
-    if constexpr (FMT == kBF32) {
-      const unsigned r1 = r + 1u;
-      const uint4 q1 = *reinterpret_cast<const uint4*>(sw + r1 * 16u + (wide_chunk(r1, c) << 2));
-      const uint32_t w1[4] = {q1.x, q1.y, q1.z, q1.w};
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const float b0 = __uint_as_float(w0[f]), b1 = __uint_as_float(w1[f]);
-        float v = fmaf(ph, b1 - b0, b0);
-        if constexpr (WGT != 0) v = __fmul_rn(ww[j], v);
-        acc[j][f] = fmaf(mm[f], v, acc[j][f]);
-      }
-    } else if constexpr (FMT == kBBF16P) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        float v = fmaf(ph, __uint_as_float(w0[f] & 0xffff0000u), __uint_as_float(w0[f] << 16));
-        if constexpr (WGT != 0) v = __fmul_rn(ww[j], v);
-        acc[j][f] = fmaf(mm[f], v, acc[j][f]);
-      }
-    } else {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&w0[f]));
-        float v = fmaf(ph, h.y, h.x);
-        if constexpr (WGT != 0) v = __fmul_rn(ww[j], v);
-        acc[j][f] = fmaf(mm[f], v, acc[j][f]);
-      }
-    }
-  }
-}
-
 // Interpolate one sensor's integrand at the lane's 4 window offsets uu (rows
 // from the start of the sensor's window at `off`) and accumulate FB frames
 // weighted by the multipliers sm (and, WGT = 1, by the per-pixel weights ww:
@@ -340,17 +257,11 @@ constexpr int kRing = 16;  // unit indices in flight between the producer and th
 // anchor per sensor copied into each stage and the pixel terms.  The computed
 // delays hold more live registers; the minimum of resident CTAs keeps the
 // compiler from spilling them (0 leaves the table variants unconstrained).
-// Pixel groups across a tile: 128 pixels per consumer warp (4 per lane), or
-// 64 (8 per lane, 4 frames each) for wide 16-frame units.
-template <int P, int FB>
-constexpr int consumer_pixel_warps() { return FB == 16 ? P / 64 : P / 128; }
-
 template <int P, int FB, int FMT, int SW, int MODE>
-__global__ void __launch_bounds__(32 * (consumer_pixel_warps<P, FB>() * SW + 3),
-                                  (MODE & 1) ? (FB == 1 ? 3 : (FB == 16 ? 1 : 2)) : 0)
+__global__ void __launch_bounds__(32 * ((P / 128) * SW + 3), (MODE & 1) ? (FB == 1 ? 3 : 2) : 0)
     gather_kernel(const __grid_constant__ StreamParams p) {
   constexpr int DELAYS = MODE & 1, WGT = (MODE >> 1) & 1;
-  constexpr int PW = consumer_pixel_warps<P, FB>();  // warps across the tile's pixels
+  constexpr int PW = P / 128;   // warps across the tile's pixels
   static_assert((SW & (SW - 1)) == 0, "sensor phases: a power of two");
   constexpr int NWC = PW * SW;  // consumer warps
   extern __shared__ __align__(128) unsigned char smem[];
@@ -578,73 +489,6 @@ __global__ void __launch_bounds__(32 * (consumer_pixel_warps<P, FB>() * SW + 3),
       const int64_t u = unit_ring[j % kRing];
       if (u < 0) break;
       const UnitPos q = decode_unit(p, u, inst);
-      if constexpr (FB == 16) {
-        // wide unit: lane (g, c) owns frames 4c..4c+3 of pixels g + 8 j
-        const int g = lane >> 2, c = lane & 3;
-        const int px = pg * 64 + g;
-        float4 pq[DELAYS || WGT ? 8 : 1];
-        if constexpr (DELAYS != 0 || WGT != 0) {
-          const float4* src = p.inst[q.inst].pix + int64_t(q.tile) * P + px;
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) pq[jj] = __ldcg(src + 8 * jj);
-        }
-        float acc[8][4];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) acc[jj][f] = 0.0f;
-        for (int s0 = q.s_lo; s0 < q.s_hi; ++seq) {
-          const int st = int(seq % p.stages);
-          if (s0 != q.s_lo && !wait_full(st)) {
-            ok = false;
-            break;
-          }
-          const int2 hdr = stage_hdr[st];
-          const int se = hdr.x;
-          // the first sensor of the stage whose phase in the segment is sp
-          const int sl0 = (sp - (s0 - q.s_lo)) & (SW - 1);
-          s0 += se;
-          const unsigned char* sb = stage0 + st * L.bytes;
-          const float* su = reinterpret_cast<const float*>(sb + L.u) + px;
-          const uint32_t* sm = reinterpret_cast<const uint32_t*>(sb + L.m) + hdr.y * FB;
-          const int* soff = reinterpret_cast<const int*>(sb + L.off);
-          const uint32_t* sw = reinterpret_cast<const uint32_t*>(sb + L.win);
-          const float4* swa = reinterpret_cast<const float4*>(sb + L.wa);
-          const float4* sa = reinterpret_cast<const float4*>(sb + L.u);
-          for (int sl = sl0; sl < se; sl += SW) {
-            float uu[8], ww[8];
-            if constexpr (DELAYS == 0) {
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) uu[jj] = su[sl * P + 8 * jj];
-            } else {
-              const float4 A = sa[2 * sl], B = sa[2 * sl + 1];
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) uu[jj] = const_delay(pq[jj], A, B);
-            }
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) ww[jj] = 1.0f;
-            if constexpr (WGT != 0) {
-              const float4 E = swa[2 * sl], N = swa[2 * sl + 1];
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) ww[jj] = solid_angle_weight(pq[jj], E, N);
-            }
-            lerp_accumulate_wide<FMT, WGT>(acc, uu, ww, sm + sl * FB, soff[sl], sw, p.Wst, c);
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&empty[st]);
-        }
-        if (!ok) break;
-        const int buf = int(j & 1);
-        if (j >= 2) red_free_sync(buf, (NWC + 1) * 32);
-        float* rb = red + size_t(buf) * SW * FB * P;
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) rb[(sp * FB + 4 * c + f) * P + px + 8 * jj] = acc[jj][f];
-        if (threadIdx.x == 0) red_unit[buf] = u;
-        red_full_arrive(buf, (NWC + 1) * 32);
-        continue;
-      }
       float4 pq[4];  // constant speed or weights: the lane's pixels relative to the tile anchor
       if constexpr (DELAYS != 0 || WGT != 0) {
         const float4* src = p.inst[q.inst].pix + int64_t(q.tile) * P + pg * 128 + lane;
@@ -735,43 +579,35 @@ __global__ void __launch_bounds__(32 * (consumer_pixel_warps<P, FB>() * SW + 3),
       const int f0 = q.fg * FB;
       const int fb_eff = min(FB, d.n_frames - f0);
       const float* rb = red + size_t(ew) * SW * FB * P;
+      float v[FB][KO];
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb)
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+          const int o = fb * P + k * 32 + lane;
+          float a = 0.0f;
+#pragma unroll
+          for (int ph = 0; ph < SW; ++ph) a += rb[ph * FB * P + o];  // fixed phase order
+          v[fb][k] = a;
+        }
+      red_free_arrive(ew, (NWC + 1) * 32);  // red[ew] free again
       int slot_idx[KO];
 #pragma unroll
       for (int k = 0; k < KO; ++k) slot_idx[k] = __ldcg(d.slot + int64_t(q.tile) * P + k * 32 + lane);
       const int64_t pbase = ((int64_t(q.fg) * d.n_tiles + q.tile) * d.n_seg) * FB * P;
-      float* mine = d.part + pbase + int64_t(q.seg) * FB * P;
-      // the unit's sums FC frames at a time (all of them when FB <= 8; 16
-      // frames of 8 outputs would take 128 registers)
-      constexpr int FC = FB > 8 ? 4 : FB;
+      if (d.n_seg == 1) {
 #pragma unroll
-      for (int fc = 0; fc < FB; fc += FC) {
-        float v[FC][KO];
+        for (int fb = 0; fb < FB; ++fb)
 #pragma unroll
-        for (int fb = 0; fb < FC; ++fb)
-#pragma unroll
-          for (int k = 0; k < KO; ++k) {
-            const int o = (fc + fb) * P + k * 32 + lane;
-            float a = 0.0f;
-#pragma unroll
-            for (int ph = 0; ph < SW; ++ph) a += rb[ph * FB * P + o];  // fixed phase order
-            v[fb][k] = a;
-          }
-        if (fc + FC == FB) red_free_arrive(ew, (NWC + 1) * 32);  // red[ew] free again
-        if (d.n_seg == 1) {
-#pragma unroll
-          for (int fb = 0; fb < FC; ++fb)
-#pragma unroll
-            for (int k = 0; k < KO; ++k)
-              if (fc + fb < fb_eff && slot_idx[k] >= 0)
-                d.out[int64_t(f0 + fc + fb) * d.out_stride + slot_idx[k]] = v[fb][k];
-        } else {
-#pragma unroll
-          for (int fb = 0; fb < FC; ++fb)
-#pragma unroll
-            for (int k = 0; k < KO; ++k) __stcg(mine + (fc + fb) * P + k * 32 + lane, v[fb][k]);
-        }
+          for (int k = 0; k < KO; ++k)
+            if (fb < fb_eff && slot_idx[k] >= 0) d.out[int64_t(f0 + fb) * d.out_stride + slot_idx[k]] = v[fb][k];
+        continue;
       }
-      if (d.n_seg == 1) continue;
+      float* mine = d.part + pbase + int64_t(q.seg) * FB * P;
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb)
+#pragma unroll
+        for (int k = 0; k < KO; ++k) __stcg(mine + fb * P + k * 32 + lane, v[fb][k]);
       // the last segment of a tile to finish sums all segments in fixed order;
       // the counter's release/acquire orders the partials of every lane (the
       // warp barrier before it makes the other lanes' stores part of the release)
@@ -824,7 +660,7 @@ static cudaError_t gather_t(const StreamParams& p, size_t smem, int grid, cudaSt
     if (e != cudaSuccess) return e;
     smem_set = smem;
   }
-  const int threads = 32 * (consumer_pixel_warps<P, FB>() * SW + 3);
+  const int threads = 32 * ((P / 128) * SW + 3);
   if (resident) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -853,7 +689,6 @@ static cudaError_t gather_fb(int FB, const StreamParams& p, size_t smem, int gri
     case 2: return gather_t<P, 2, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
     case 4: return gather_t<P, 4, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
     case 8: return gather_t<P, 8, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
-    case 16: return gather_t<P, 16, FMT, SW, MODE>(p, smem, grid, st, resident, n_sm);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -884,7 +719,6 @@ static const void* gather_func_fb(int FB) {
     case 2: return reinterpret_cast<const void*>(gather_kernel<P, 2, FMT, SW, MODE>);
     case 4: return reinterpret_cast<const void*>(gather_kernel<P, 4, FMT, SW, MODE>);
     case 8: return reinterpret_cast<const void*>(gather_kernel<P, 8, FMT, SW, MODE>);
-    case 16: return reinterpret_cast<const void*>(gather_kernel<P, 16, FMT, SW, MODE>);
   }
   return nullptr;
 }

@@ -2,8 +2,8 @@
 //
 // Two launches.  The gather kernel is persistent: CTA c takes units (tile,
 // segment of G sensors) c, c + grid, c + 2 grid, ... in tile-major order, and
-// (constant speed, or signals read from host memory) asks L2 for each unit's
-// delay data two units ahead with one bulk prefetch.
+// (constant speed) asks L2 for each unit's delay data two units ahead with one
+// bulk prefetch.
 // Its warps are the (pixel group, sensor phase) pairs of the staged kernel's
 // consumers; a warp reads the delay data (table offsets, or the constant-
 // speed anchors) and the window bases for a chunk of its sensors, then
@@ -115,19 +115,14 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
   const int pg = warp % PW, sp = warp / PW;
   const int px0 = pg * 128 + lane;
   const int64_t n_units = int64_t(p.n_tiles) * p.n_seg;
-  // Delay data is pulled into L2 ahead of use for constant speed, and for a
-  // stored table when the preprocessing reads the signals from host memory
-  // (the host round trip): the table stream then overlaps that slow read
-  // instead of following it.
-  const bool pf = DELAYS != 0 || p.host_status != nullptr;
-  if (pf && threadIdx.x == 0) {
+  if (DELAYS != 0 && threadIdx.x == 0) {
     prefetch_unit<P, DELAYS>(p, blockIdx.x, n_units);
     prefetch_unit<P, DELAYS>(p, int64_t(blockIdx.x) + gridDim.x, n_units);
   }
   const uint32_t* bsrc = static_cast<const uint32_t*>(p.b);
   bool waited = false;
   for (int64_t unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
-    if (pf && threadIdx.x == 0)
+    if (DELAYS != 0 && threadIdx.x == 0)
       prefetch_unit<P, DELAYS>(p, unit + 2 * int64_t(gridDim.x), n_units);
     const int tile = int(unit / p.n_seg);
     const int seg = int(unit - int64_t(tile) * p.n_seg);

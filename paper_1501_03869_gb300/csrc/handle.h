@@ -50,8 +50,8 @@ struct pat_bp_s {
   int pre_fb = 1;                     // their frames per group
   int wst_cache[33] = {0};            // stage window bound per sensors-per-stage
   // launch shapes chosen by the autotuner: [frames-per-group index][format]
-  int tuned_S[5][3] = {};
-  int tuned_budget_kb[5][3] = {};
+  int tuned_S[4][3] = {};
+  int tuned_budget_kb[4][3] = {};
   float* d_u = nullptr;               // table offsets (delays == 0)
   float* d_anchor = nullptr;          // per (tile, sensor) anchors (delays == 1)
   float4* d_pix = nullptr;            // per-pixel terms (delays == 1 or wgt)

@@ -63,15 +63,19 @@ __device__ __forceinline__ void load_run8(const void* sig, int64_t row0, int k0,
   }
 }
 
+// The 16-bit (value, slope) pair of b_k and b_{k+1} scaled by inv: every
+// product and difference is explicitly rounded, so the codes do not depend on
+// how the compiler contracts the expression in the kernel that calls this.
 template <int FMT>
-__device__ __forceinline__ uint32_t encode_pair(float v0, float v1) {
+__device__ __forceinline__ uint32_t encode_pair(float b0, float b1, float inv) {
+  const float v0 = __fmul_rn(b0, inv), v1 = __fmul_rn(b1, inv);
   if constexpr (FMT == kBBF16P) {
     const __nv_bfloat16 q0 = __float2bfloat16_rn(v0);
-    const __nv_bfloat16 q1 = __float2bfloat16_rn(v1 - __bfloat162float(q0));
+    const __nv_bfloat16 q1 = __float2bfloat16_rn(__fsub_rn(v1, __bfloat162float(q0)));
     return uint32_t(__bfloat16_as_ushort(q0)) | (uint32_t(__bfloat16_as_ushort(q1)) << 16);
   } else {
     const __half q0 = __float2half_rn(v0);
-    const __half q1 = __float2half_rn(v1 - __half2float(q0));
+    const __half q1 = __float2half_rn(__fsub_rn(v1, __half2float(q0)));
     return uint32_t(__half_as_ushort(q0)) | (uint32_t(__half_as_ushort(q1)) << 16);
   }
 }
@@ -173,48 +177,25 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
     }
   }
   uint32_t* dst = static_cast<uint32_t*>(p.b) + (int64_t(g) * p.n_sensors + s) * p.n_t_pad * FB;
-  // Rows of 16 frames are formed 8 frames at a time (registers), and their
-  // four 16-byte chunks are stored rotated as the gather's wide units read
-  // them: chunk c of row k sits at chunk c ^ ((k / 2) mod 4).  The runs start
-  // at multiples of 8 rows, so row k0 + j rotates by (j / 2) mod 4.
-  constexpr int FH = FB > 8 ? 8 : FB;
   for (int kw = (threadIdx.x & ~31) * K; kw < p.n_t_pad; kw += blockDim.x * K) {
     const int k0 = kw + lane * K;
+    uint32_t w[K * FB];
 #pragma unroll
-    for (int h = 0; h < FB; h += FH) {
-      uint32_t w[K * FH];
-#pragma unroll
-      for (int fl = 0; fl < FH; ++fl) {
-        const int fb = h + fl;
-        if (fb < fb_eff) {
-          float b[K + 1];
-          b_run(fb, k0, b);
-#pragma unroll
-          for (int j = 0; j < K; ++j) {
-            if constexpr (FMT == kBF32) w[j * FH + fl] = __float_as_uint(b[j]);
-            else w[j * FH + fl] = encode_pair<FMT>(b[j] * inv[fb], b[j + 1] * inv[fb]);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < K; ++j) w[j * FH + fl] = 0u;
-        }
-      }
-      if (k0 >= p.n_t_pad) continue;
-      if constexpr (FB <= 8) {
-        store_words<K * FB>(dst + int64_t(k0) * FB, w);
-      } else {
+    for (int fb = 0; fb < FB; ++fb) {
+      if (fb < fb_eff) {
+        float b[K + 1];
+        b_run(fb, k0, b);
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          const int rot = (j >> 1) & 3;
-          const int m = (h >> 3) ^ (rot >> 1);  // the 32-byte half this pass's two chunks go to
-          uint32_t* row = dst + (int64_t(k0) + j) * FB + 8 * m;
-          const uint4 a = make_uint4(w[j * 8 + 0], w[j * 8 + 1], w[j * 8 + 2], w[j * 8 + 3]);
-          const uint4 b4 = make_uint4(w[j * 8 + 4], w[j * 8 + 5], w[j * 8 + 6], w[j * 8 + 7]);
-          *reinterpret_cast<uint4*>(row) = (rot & 1) ? b4 : a;
-          *reinterpret_cast<uint4*>(row + 4) = (rot & 1) ? a : b4;
+          if constexpr (FMT == kBF32) w[j * FB + fb] = __float_as_uint(b[j]);
+          else w[j * FB + fb] = encode_pair<FMT>(b[j], b[j + 1], inv[fb]);
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j * FB + fb] = 0u;
       }
     }
+    if (k0 < p.n_t_pad) store_words<K * FB>(dst + int64_t(k0) * FB, w);
   }
   if (threadIdx.x < FB) {
     const int fb = threadIdx.x;
@@ -226,11 +207,104 @@ __device__ __forceinline__ void preprocess_row(const PreParams& p, int s, int g)
   }
 }
 
+// The same rows for FB >= 2 frames per group, laid out for occupancy: thread
+// t works on frame t mod FB and runs of 8 samples, frames fastest across the
+// lanes, so a run's neighbouring runs of the same frame sit FB lanes away
+// (shuffles by FB), every store instruction writes whole 32-byte pieces of
+// FB * 8 consecutive words, and a thread keeps 11 samples instead of FB x 11.
+// Each sample is the same expression as in preprocess_row, so the integrand
+// has the same bits whatever the frames per group.
+template <int DT, int FMT, int FB>
+__device__ __forceinline__ void preprocess_row_frames(const PreParams& p, int s, int g) {
+  static_assert(FB >= 2 && FB <= 16 && (FB & (FB - 1)) == 0, "frames per group");
+  constexpr int K = 8;
+  constexpr int RUNS = 256 / FB;  // runs of one frame per block pass
+  __shared__ float red[8][FB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int fb = threadIdx.x & (FB - 1);
+  const int run = threadIdx.x / FB;
+  const int f0 = g * FB;
+  const int fb_eff = min(FB, p.n_frames - f0);
+  const int n = p.n_t;
+  const int f = min(f0 + fb, p.n_frames - 1);
+  const int64_t r = int64_t(f) * p.n_sensors + s;
+  const int64_t row0 = r * n;
+  const float sc = p.scales ? p.scales[r] : 1.0f;
+  auto sample = [&](int k) {
+    return (k >= 0 && k < n) ? __fmul_rn(load_sample<DT>(p.sig, row0 + k), sc) : 0.0f;
+  };
+  // b_{k0..k0+K} of this thread's frame; all lanes of a warp call it together
+  auto b_run = [&](int k0, float (&b)[K + 1]) {
+    float v[K + 3];  // p_{k0-1} .. p_{k0+K+1}
+    load_run8<DT>(p.sig, row0, k0, n, sc, v + 1);
+    const float prev = __shfl_up_sync(0xffffffffu, v[K], FB);
+    const float nx1 = __shfl_down_sync(0xffffffffu, v[1], FB);
+    const float nx2 = __shfl_down_sync(0xffffffffu, v[2], FB);
+    v[0] = lane < FB ? sample(k0 - 1) : prev;
+    v[K + 1] = lane >= 32 - FB ? sample(k0 + K) : nx1;
+    v[K + 2] = lane >= 32 - FB ? sample(k0 + K + 1) : nx2;
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const int k = k0 + j;
+      float x;
+      if (k >= n) x = 0.0f;
+      else if (k == 0) x = 2.0f * v[j + 1];
+      else if (k == n - 1) x = fmaf(-2.0f * float(k), __fsub_rn(v[j + 1], v[j]), 2.0f * v[j + 1]);
+      else x = fmaf(-float(k), __fsub_rn(v[j + 2], v[j]), 2.0f * v[j + 1]);
+      b[j] = x;
+    }
+  };
+  float sigma = 1.0f, inv = 1.0f;
+  if constexpr (FMT != kBF32) {
+    float mx = 0.0f;
+    for (int kw = 0; kw < n; kw += RUNS * K) {
+      const int k0 = kw + run * K;  // runs past the row give b = 0
+      float b[K + 1];
+      b_run(k0, b);
+#pragma unroll
+      for (int j = 0; j < K; ++j) mx = fmaxf(mx, fabsf(b[j]));
+    }
+    for (int o = FB; o < 32; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane < FB) red[warp][lane] = mx;
+    __syncthreads();
+    float v = 0.0f;
+    for (int q = 0; q < int(blockDim.x >> 5); ++q) v = fmaxf(v, red[q][fb]);
+    sigma = v > 0.0f ? v : 1.0f;
+    inv = 1.0f / sigma;
+  }
+  uint32_t* dst = static_cast<uint32_t*>(p.b) + (int64_t(g) * p.n_sensors + s) * p.n_t_pad * FB;
+  const bool live = fb < fb_eff;
+  for (int kw = 0; kw < p.n_t_pad; kw += RUNS * K) {
+    const int k0 = kw + run * K;
+    float b[K + 1];
+    b_run(k0, b);
+    if (k0 >= p.n_t_pad) continue;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      uint32_t wv = 0u;
+      if (live) {
+        if constexpr (FMT == kBF32) wv = __float_as_uint(b[j]);
+        else wv = encode_pair<FMT>(b[j], b[j + 1], inv);
+      }
+      dst[int64_t(k0 + j) * FB + fb] = wv;
+    }
+  }
+  if (threadIdx.x < FB) p.m[(int64_t(g) * p.n_sensors_pad + s) * FB + fb] = live ? p.weights[s] * sigma : 0.0f;
+}
+
+// One (sensor, frame group) row per CTA: the frame-fast layout for groups of
+// several frames, the sample-run layout (preprocess_row) for single frames.
+template <int DT, int FMT, int FB>
+__device__ __forceinline__ void preprocess_group(const PreParams& p, int s, int g) {
+  if constexpr (FB == 1) preprocess_row<DT, FMT, FB>(p, s, g);
+  else preprocess_row_frames<DT, FMT, FB>(p, s, g);
+}
+
 template <int DT, int FMT, int FB>
 __global__ void __launch_bounds__(256) preprocess_kernel(const PreParams p) {
   // let the gather that depends on this kernel start its prologue now
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  preprocess_row<DT, FMT, FB>(p, blockIdx.x, blockIdx.y);
+  preprocess_group<DT, FMT, FB>(p, blockIdx.x, blockIdx.y);
 }
 
 // Several instances in one launch: CTA x belongs to the instance whose range
@@ -247,7 +321,7 @@ __global__ void __launch_bounds__(256) preprocess_multi_kernel(const __grid_cons
   }
   const PreParams& q = p.inst[lo];
   const int64_t loc = x - p.cta_begin[lo];
-  preprocess_row<DT, FMT, FB>(q, int(loc % q.n_sensors), int(loc / q.n_sensors));
+  preprocess_group<DT, FMT, FB>(q, int(loc % q.n_sensors), int(loc / q.n_sensors));
 }
 
 
@@ -275,7 +349,7 @@ __global__ void wait_probe_kernel(int* status, uint64_t timeout_ns) {
 }
 
 // --------------------------------------------------------------- launchers --
-int gather_threads(const GatherConfig& c) { return 32 * ((c.FB == 16 ? c.P / 64 : c.P / 128) * c.SW + 3); }
+int gather_threads(const GatherConfig& c) { return 32 * ((c.P / 128) * c.SW + 3); }
 
 size_t gather_smem_bytes(const GatherConfig& c, int Wst) {
   const StageLayout L(c.S, c.P, c.FB, Wst, c.delays | (c.wgt << 1));
@@ -290,7 +364,6 @@ static cudaError_t launch_pre_fb(const PreParams& p, cudaStream_t st) {
     case 2: preprocess_kernel<DT, FMT, 2><<<grid, 256, 0, st>>>(p); break;
     case 4: preprocess_kernel<DT, FMT, 4><<<grid, 256, 0, st>>>(p); break;
     case 8: preprocess_kernel<DT, FMT, 8><<<grid, 256, 0, st>>>(p); break;
-    case 16: preprocess_kernel<DT, FMT, 16><<<grid, 256, 0, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -306,7 +379,6 @@ static cudaError_t launch_pre_multi_fb(const PreMultiParams& p, cudaStream_t st)
     case 2: preprocess_multi_kernel<DT, FMT, 2><<<grid, 256, 0, st>>>(p); break;
     case 4: preprocess_multi_kernel<DT, FMT, 4><<<grid, 256, 0, st>>>(p); break;
     case 8: preprocess_multi_kernel<DT, FMT, 8><<<grid, 256, 0, st>>>(p); break;
-    case 16: preprocess_multi_kernel<DT, FMT, 16><<<grid, 256, 0, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -377,7 +449,6 @@ static const void* pre_multi_func_fb(int FB) {
     case 2: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 2>);
     case 4: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 4>);
     case 8: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 8>);
-    case 16: return reinterpret_cast<const void*>(preprocess_multi_kernel<DT, FMT, 16>);
   }
   return nullptr;
 }

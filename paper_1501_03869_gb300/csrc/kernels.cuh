@@ -81,7 +81,7 @@ struct StreamParams {
 
 struct GatherConfig {
   int P = 128;      // pixels per tile
-  int FB = 1;       // frames per unit (1, 2, 4, 8, 16)
+  int FB = 1;       // frames per unit (1, 2, 4, 8)
   int SW = 4;       // sensor-phase warps
   int S = 16;       // sensors per stage
   int stages = 4;

@@ -368,10 +368,10 @@ namespace patbp {
 int fmt_for(pat_dtype dt) { return dt == PAT_F32 ? kBF32 : (dt == PAT_BF16 ? kBBF16P : kBF16P); }
 
 int frames_per_group(int n_frames) {
-  return n_frames >= 16 ? 16 : (n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1)));
+  return n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1));
 }
 
-int fb_index(int FB) { return FB == 1 ? 0 : (FB == 2 ? 1 : (FB == 4 ? 2 : (FB == 8 ? 3 : 4))); }
+int fb_index(int FB) { return FB == 1 ? 0 : (FB == 2 ? 1 : (FB == 4 ? 2 : 3)); }
 
 static pat_status grow_zeroed(void** p, size_t* cap, size_t need, const char* what) {
   if (need <= *cap) return PAT_OK;

@@ -3,10 +3,10 @@
 // Every instance (one speed map's table, Sec. III) contributes its units of
 // work to a persistent gather launch.  Instances are grouped by the frames
 // that share one pass over a table tile (FB: the largest power of two up to
-// 16 not above the instance's frame count), and every group ("class") has its
+// 8 not above the instance's frame count), and every group ("class") has its
 // own preprocessing launch (the Eq. (BP) integrand of all its instances) and
 // its own gather launch; all preprocessing launches go first, then the
-// gathers.  A 16-frame instance therefore streams its table once, while a
+// gathers.  A 16-frame instance therefore streams its table twice, while a
 // single-frame instance next to it does not pay for frames it does not have.
 // A plan can replay the launches as a CUDA graph whose kernel-node parameters
 // are refreshed per execution, and can time candidate launch shapes once

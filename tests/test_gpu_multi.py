@@ -48,7 +48,7 @@ def test_plan_tuned_graph_matches_single_handles(c4):
     info = plan.info
     assert info["tuned"] == 1 and info["graph"] == 1 and info["n_inst"] == 32
     # one class per frames-per-unit value the instances' frame counts give
-    fbs = {min(16, 1 << (w.n_frames.bit_length() - 1)) for w in ws}
+    fbs = {min(8, 1 << (w.n_frames.bit_length() - 1)) for w in ws}
     assert info["n_classes"] == len(fbs) and info["fb_mask"] == sum(fbs)
     assert info["frames_per_unit"] == max(fbs)
     for i, o in enumerate(outs):
