@@ -431,8 +431,10 @@ def serving_form(args):
         scl = torch.empty(sc.shape, dtype=torch.float32, pin_memory=True).numpy()
         scl[:] = sc
         inp.append((c, scl))
+    # results go to a ring of 256 page-locked images (9.8 MB each): a request
+    # waits for the ring slot's previous request, so at most 256 are queued
     ring = [torch.empty(subs[0].speed.shape, dtype=torch.float32, pin_memory=True).numpy()
-            for _ in range(64)]
+            for _ in range(256)]
     ring_t = [None] * len(ring)
     rng = np.random.default_rng(5)
 

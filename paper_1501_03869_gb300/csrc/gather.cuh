@@ -77,6 +77,28 @@ __device__ __forceinline__ void solid_angle_weights(float (&ww)[4], const float4
   for (int x = 0; x < 4; ++x) ww[x] = solid_angle_weight(pq[x], E, N);
 }
 
+// Rows of 8 frames (32 bytes, four to a 128-byte line of shared-memory banks)
+// are stored with their two 16-byte halves swapped when bit 2 of the row index
+// is set.  The 8 lanes of a 16-byte load phase read rows of 8 pixels; without
+// the swap two of them conflict whenever their rows agree mod 4, with it only
+// when they agree mod 8.  Windows start at rows that are multiples of 8 in
+// global and shared memory, so a row's swap is the same in both.
+__device__ __forceinline__ void load_row8(const uint32_t* sw, unsigned r, uint32_t (&w)[8]) {
+  const unsigned x = (r >> 2) & 1u;
+  const uint4 lo = *reinterpret_cast<const uint4*>(sw + r * 8u + 4u * x);
+  const uint4 hi = *reinterpret_cast<const uint4*>(sw + r * 8u + 4u * (x ^ 1u));
+  w[0] = lo.x; w[1] = lo.y; w[2] = lo.z; w[3] = lo.w;
+  w[4] = hi.x; w[5] = hi.y; w[6] = hi.z; w[7] = hi.w;
+}
+
+// Frames fb of row r of a window in shared memory (FB words per row; 8-frame
+// rows as load_row8 describes).
+template <int FB>
+__device__ __forceinline__ void load_row(const uint32_t* sw, unsigned r, uint32_t (&w)[FB]) {
+  if constexpr (FB == 8) load_row8(sw, r, w);
+  else load_words<FB>(sw + size_t(r) * FB, w);
+}
+
 // Interpolate one sensor's integrand at the lane's 4 window offsets uu (rows
 // from the start of the sensor's window at `off`) and accumulate FB frames
 // weighted by the multipliers sm (and, WGT = 1, by the per-pixel weights ww:
@@ -98,12 +120,12 @@ __device__ __forceinline__ void lerp_accumulate(float (&acc)[FB][4], const float
   for (int x = 0; x < 4; ++x) {
     const unsigned i = min(unsigned(__float2int_rz(uu[x])), lim);
     const float ph = uu[x] - float(i);
-    const uint32_t* row = sw + size_t(i + unsigned(off)) * FB;
+    const unsigned r = i + unsigned(off);
     uint32_t w0[FB];
-    load_words<FB>(row, w0);
+    load_row<FB>(sw, r, w0);
     if constexpr (FMT == kBF32) {
       uint32_t w1[FB];
-      load_words<FB>(row + FB, w1);
+      load_row<FB>(sw, r + 1u, w1);
 #pragma unroll
       for (int fb = 0; fb < FB; ++fb) {
         const float b0 = __uint_as_float(w0[fb]), b1 = __uint_as_float(w1[fb]);

@@ -286,7 +286,11 @@ __device__ __forceinline__ void preprocess_row_frames(const PreParams& p, int s,
         if constexpr (FMT == kBF32) wv = __float_as_uint(b[j]);
         else wv = encode_pair<FMT>(b[j], b[j + 1], inv);
       }
-      dst[int64_t(k0 + j) * FB + fb] = wv;
+      // 8-frame rows: the two 16-byte halves of rows with bit 2 of the row
+      // index set are stored swapped (k0 is a multiple of 8, so that bit is
+      // j's), which the gather's shared-memory reads undo (row_half_swap)
+      const int pos = FB == 8 ? (fb ^ (((j >> 2) & 1) << 2)) : fb;
+      dst[int64_t(k0 + j) * FB + pos] = wv;
     }
   }
   if (threadIdx.x < FB) p.m[(int64_t(g) * p.n_sensors_pad + s) * FB + fb] = live ? p.weights[s] * sigma : 0.0f;

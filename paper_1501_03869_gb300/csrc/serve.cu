@@ -192,6 +192,15 @@ void reap(pat_srv_t s, std::unique_lock<std::mutex>& lk) {
   if (any) s->cv_done.notify_all();
 }
 
+// Working buffers for the largest batch, allocated while the subject becomes
+// resident: a batch never grows them later, because the cudaFree of a growth
+// would synchronise the device and stall every batch in flight.  They cover
+// every smaller batch too (n frames in groups of FB take at most as much).
+pat_status reserve_batch_buffers(pat_srv_t s, pat_bp_t h) {
+  const int F = s->cfg.max_batch_frames;
+  return ensure_buffers_fb(h, F, frames_per_group(F));
+}
+
 // Make subject k resident within the budget, evicting least recently used idle
 // subjects.  PAT_ERR_BUSY: not now (others busy); PAT_ERR_OOM: never fits.
 pat_status admit(pat_srv_t s, int k, cudaStream_t st) {
@@ -212,8 +221,9 @@ pat_status admit(pat_srv_t s, int k, cudaStream_t st) {
     ++s->evictions;
   }
   pat_status e = restore_locked(h, st);
-  if (e == PAT_OK) ++s->uploads;
-  return e;
+  if (e != PAT_OK) return e;
+  ++s->uploads;
+  return reserve_batch_buffers(s, h);
 }
 
 // Launch one batch of subject k's pending requests (same dtype) on slot sl.
@@ -397,7 +407,12 @@ extern "C" pat_status pat_srv_register(pat_srv_t s, const float* speed_host, con
   if (st != PAT_OK) return st;
   std::lock_guard<std::mutex> lk(s->mu);
   // resident until the scheduler needs the room: account it now
-  if (resident_total(s) + subject_need(s, h) > s->budget) evict_locked(h);
+  if (resident_total(s) + subject_need(s, h) > s->budget) {
+    evict_locked(h);
+  } else if ((st = reserve_batch_buffers(s, h)) != PAT_OK) {
+    pat_bp_destroy(h);
+    return st;
+  }
   s->subjects.push_back(Subject{h, 0, false});
   *subject_id = int(s->subjects.size()) - 1;
   return PAT_OK;
