@@ -389,8 +389,12 @@ typedef struct {
 pat_status pat_srv_create(size_t hbm_budget, const pat_srv_cfg* cfg, pat_srv_t* out);
 
 /* pat_srv_register -- arguments of pat_bp_create; builds the subject's table
- * (host fast marching) and keeps a pinned host copy for reloads.  The table
- * is uploaded when a request needs it.  Blocking. */
+ * (host fast marching, or the GPU solver with PAT_FLAG_GPU_TABLE) and keeps a
+ * pinned host copy for reloads.  The subject stays resident, with its working
+ * buffers for a full batch, if the budget allows; else it is evicted and
+ * uploaded when a request needs it.  Every request slot's device staging is
+ * sized for a full batch of the subject here, so serving never grows it.
+ * Blocking (an allocation can wait for batches in flight). */
 pat_status pat_srv_register(pat_srv_t srv, const float* speed_host, const pat_grid* grid,
                             const double* sensors_host, int n_sensors, const uint8_t* mask_host,
                             const float* weights_host, double dt, int n_samples, unsigned flags,

@@ -98,7 +98,12 @@ struct pat_bp_s {
 
 namespace patbp {
 
+// Fewer frames than this go through the unstaged single-frame kernels, one
+// frame after the other.
+constexpr int kStagedMinFrames = 4;
 int frames_per_group(int n_frames);
+// frames per unit a handle's reconstruction of n_frames uses (1 below kStagedMinFrames)
+int frames_per_unit(pat_bp_t h, int n_frames);
 int fb_index(int FB);
 int fmt_for(pat_dtype dt);
 // device buffers for n_frames frames grouped by FB (grown, zero-filled)
@@ -128,6 +133,9 @@ pat_status reconstruct_locked(pat_bp_t h, const void* signals_dev, pat_dtype dty
                               cudaStream_t stream, int* host_status = nullptr,
                               bool* exported = nullptr);
 pat_status restore_locked(pat_bp_t h, cudaStream_t st);
+// evict an idle handle by giving its device buffers to an evicted handle of the
+// same sizes (no synchronisation or allocation); false if the sizes differ
+bool donate_buffers_locked(pat_bp_t from, pat_bp_t to);
 // resident gather CTAs for a config (cached per config)
 int resident_ctas(const GatherConfig& c, int fmt, int wst, int n_sm);
 

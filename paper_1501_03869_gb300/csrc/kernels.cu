@@ -435,8 +435,23 @@ cudaError_t launch_gather(const GatherConfig& c, int fmt, const StreamParams& p,
     if (p.inst[i].G % p.S || p.inst[i].G > kMaxG || p.inst[i].Wst > p.Wst) return cudaErrorInvalidValue;
   if (p.n_units == 0) return cudaSuccess;
   if (c.direct) {
-    if (p.n_inst != 1) return cudaErrorInvalidValue;
-    return launch_gather_direct(c, fmt, p.inst[0], c.n_sm, p.status, p.host_status, p.timeout_ns, st);
+    // one frame after the other: frame f's integrand rows and multipliers are
+    // frame group f of the one-frame-per-group layout; the phase sums are reused
+    if (p.n_inst != 1 || c.FB != 1) return cudaErrorInvalidValue;
+    const InstDesc& d = p.inst[0];
+    const size_t word = 4;  // integrand words are 32-bit in every format
+    for (int f = 0; f < d.n_frames; ++f) {
+      InstDesc df = d;
+      df.n_frames = 1;
+      df.n_fg = 1;
+      df.b = static_cast<const unsigned char*>(d.b) + size_t(f) * d.n_sensors * d.n_t_pad * word;
+      df.m = d.m + size_t(f) * d.n_sensors_pad;
+      df.out = d.out + int64_t(f) * d.out_stride;
+      cudaError_t e = launch_gather_direct(c, fmt, df, c.n_sm, p.status,
+                                           f + 1 == d.n_frames ? p.host_status : nullptr, p.timeout_ns, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   return gather_dispatch(c, fmt, p, grid, st, nullptr, 0);
 }

@@ -371,6 +371,11 @@ int frames_per_group(int n_frames) {
   return n_frames >= 8 ? 8 : (n_frames >= 4 ? 4 : (n_frames >= 2 ? 2 : 1));
 }
 
+int frames_per_unit(pat_bp_t h, int n_frames) {
+  if (n_frames < kStagedMinFrames && !(h->flags & PAT_FLAG_STAGED_SINGLE)) return 1;
+  return frames_per_group(n_frames);
+}
+
 int fb_index(int FB) { return FB == 1 ? 0 : (FB == 2 ? 1 : (FB == 4 ? 2 : 3)); }
 
 static pat_status grow_zeroed(void** p, size_t* cap, size_t need, const char* what) {
@@ -475,9 +480,11 @@ GatherConfig config_for(pat_bp_t h, int FB, int S, size_t budget, int* wst) {
 // frames share a unit.  No choice here changes the summation order.
 GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst) {
   const size_t limit = size_t(h->max_smem);
-  if (n_frames == 1 && !(h->flags & PAT_FLAG_STAGED_SINGLE)) {
-    // one frame: the unstaged kernels (same arithmetic and order as the
-    // staged kernel with one frame per unit)
+  if (n_frames < kStagedMinFrames && !(h->flags & PAT_FLAG_STAGED_SINGLE)) {
+    // up to 3 frames: the unstaged kernels, one frame after the other (same
+    // arithmetic and order as the staged kernel); units of 1 or 2 frames make
+    // the staged kernel's window copies too small to pay (measured slower per
+    // frame on the 3-D subject)
     GatherConfig c = config_for(h, 1, 16, 72 * 1024, wst);
     c.direct = 1;
     return c;
@@ -612,6 +619,7 @@ pat_status evict_locked(pat_bp_t h) {
 
 pat_status restore_locked(pat_bp_t h, cudaStream_t st) {
   if (!h->evicted) return PAT_OK;
+  // buffers already present (handed over by donate_buffers_locked) are reused
   void** dev[pat_bp_s::kMirrors] = {
       h->delays ? reinterpret_cast<void**>(&h->d_anchor) : reinterpret_cast<void**>(&h->d_u),
       reinterpret_cast<void**>(&h->d_base), reinterpret_cast<void**>(&h->d_slot),
@@ -619,7 +627,7 @@ pat_status restore_locked(pat_bp_t h, cudaStream_t st) {
       reinterpret_cast<void**>(&h->d_pix), reinterpret_cast<void**>(&h->d_wanchor)};
   for (int i = 0; i < pat_bp_s::kMirrors; ++i) {
     if (!h->mirror[i]) continue;
-    if (cudaMalloc(dev[i], h->mirror_bytes[i]) != cudaSuccess) {
+    if (!*dev[i] && cudaMalloc(dev[i], h->mirror_bytes[i]) != cudaSuccess) {
       for (int j = 0; j <= i; ++j) {
         cudaFree(*dev[j]);
         *dev[j] = nullptr;
@@ -630,6 +638,46 @@ pat_status restore_locked(pat_bp_t h, cudaStream_t st) {
   }
   h->evicted = false;
   return PAT_OK;
+}
+
+// Evict `from` (idle: none of its work in flight) by handing its device
+// buffers to the evicted handle `to`, whose reload then fills them instead of
+// allocating: no device synchronisation, no cudaFree, no cudaMalloc.  Only for
+// handles whose table buffers have the same sizes (same layout kind); false
+// (nothing changed) otherwise.
+bool donate_buffers_locked(pat_bp_t from, pat_bp_t to) {
+  if (from == to || from->evicted || !to->evicted || !from->mirror[0] || !to->mirror[0]) return false;
+  if (from->delays != to->delays || from->wgt != to->wgt || from->device != to->device) return false;
+  for (int i = 0; i < pat_bp_s::kMirrors; ++i)
+    if (from->mirror_bytes[i] != to->mirror_bytes[i] || !from->mirror[i] != !to->mirror[i]) return false;
+  void** src[pat_bp_s::kMirrors] = {
+      from->delays ? reinterpret_cast<void**>(&from->d_anchor) : reinterpret_cast<void**>(&from->d_u),
+      reinterpret_cast<void**>(&from->d_base), reinterpret_cast<void**>(&from->d_slot),
+      reinterpret_cast<void**>(&from->d_zero_runs), reinterpret_cast<void**>(&from->d_w),
+      reinterpret_cast<void**>(&from->d_pix), reinterpret_cast<void**>(&from->d_wanchor)};
+  void** dst[pat_bp_s::kMirrors] = {
+      to->delays ? reinterpret_cast<void**>(&to->d_anchor) : reinterpret_cast<void**>(&to->d_u),
+      reinterpret_cast<void**>(&to->d_base), reinterpret_cast<void**>(&to->d_slot),
+      reinterpret_cast<void**>(&to->d_zero_runs), reinterpret_cast<void**>(&to->d_w),
+      reinterpret_cast<void**>(&to->d_pix), reinterpret_cast<void**>(&to->d_wanchor)};
+  for (int i = 0; i < pat_bp_s::kMirrors; ++i) {
+    if (!from->mirror[i]) continue;
+    *dst[i] = *src[i];
+    *src[i] = nullptr;
+  }
+  // working buffers: the counters must read zero, which they do between
+  // launches (every launch returns them to zero)
+  std::swap(to->d_b, from->d_b);
+  std::swap(to->b_cap, from->b_cap);
+  std::swap(to->d_m, from->d_m);
+  std::swap(to->m_cap, from->m_cap);
+  std::swap(to->d_part, from->d_part);
+  std::swap(to->part_cap, from->part_cap);
+  std::swap(to->d_counter, from->d_counter);
+  std::swap(to->counter_cap, from->counter_cap);
+  from->pre_frames = 0;
+  from->evicted = true;
+  return true;
 }
 
 }  // namespace patbp

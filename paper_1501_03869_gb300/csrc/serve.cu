@@ -4,7 +4,9 @@
 // single-frame requests for several subjects (speed maps):
 //   * admission: a subject's table (and working buffers) must be resident to
 //     run; tables live within an HBM budget, the least recently used idle
-//     subject is evicted to its pinned host copy when room is needed;
+//     subject is evicted to its pinned host copy when room is needed (its
+//     device buffers handed straight to the incoming subject when their sizes
+//     match, so the reload is only the upload);
 //   * batching: the pending frames of one subject (same dtype, arrival order,
 //     up to max_batch_frames) go in one reconstruction;
 //   * continuous batching: batches of different subjects run concurrently on
@@ -216,8 +218,12 @@ pat_status admit(pat_srv_t s, int k, cudaStream_t st) {
       if (victim < 0 || c.last_use < s->subjects[victim].last_use) victim = i;
     }
     if (victim < 0) return PAT_ERR_BUSY;
-    pat_status e = evict_locked(s->subjects[victim].h);
-    if (e != PAT_OK) return e;
+    // an idle victim of the same sizes hands its buffers over (no device
+    // synchronisation, free or allocation); any other is evicted normally
+    if (!donate_buffers_locked(s->subjects[victim].h, h)) {
+      pat_status e = evict_locked(s->subjects[victim].h);
+      if (e != PAT_OK) return e;
+    }
     ++s->evictions;
   }
   pat_status e = restore_locked(h, st);
@@ -406,6 +412,20 @@ extern "C" pat_status pat_srv_register(pat_srv_t s, const float* speed_host, con
                                 n_samples, flags | PAT_FLAG_HOST_MIRROR, &h);
   if (st != PAT_OK) return st;
   std::lock_guard<std::mutex> lk(s->mu);
+  // every slot's staging for a full batch of this subject (FP32 signals, the
+  // largest), so no batch grows them later: a growth's cudaFree would
+  // synchronise the device and stall the batches in flight
+  {
+    const size_t F = size_t(s->cfg.max_batch_frames);
+    for (Slot& sl : s->slots) {
+      if ((st = grow_dev(&sl.d_sig, &sl.sig_cap, F * h->ns * h->nt * 4)) != PAT_OK ||
+          (st = grow_dev(reinterpret_cast<void**>(&sl.d_sc), &sl.sc_cap, F * h->ns * 4)) != PAT_OK ||
+          (st = grow_dev(reinterpret_cast<void**>(&sl.d_out), &sl.out_cap, F * size_t(h->out_stride) * 4)) != PAT_OK) {
+        pat_bp_destroy(h);
+        return st;
+      }
+    }
+  }
   // resident until the scheduler needs the room: account it now
   if (resident_total(s) + subject_need(s, h) > s->budget) {
     evict_locked(h);
