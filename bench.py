@@ -151,10 +151,22 @@ def kernel_source_hash():
     """Hash of the sources of the single-frame gather (the kernel the roofline
     line is about); a committed traffic record is used only while it matches."""
     h = hashlib.sha256()
-    for fn in ("gather_direct.cu", "gather.cuh", "kernels.cuh"):
+    for fn in ("gather_direct.cu", "gather.cuh", "kernels.cuh", "device.cuh"):
         with open(os.path.join(ROOT, "paper_1501_03869_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def single_frame_kernels(info):
+    """Names of the two kernels one FP32 frame of a stored table takes: the
+    windowed gather when every window fits its largest slot (288 rows)."""
+    P = info["tile_pix"]
+    sw = 4 if P == 128 else 2
+    W = info["window"]
+    if W <= 288:
+        wb = 128 if W <= 128 else (192 if W <= 192 else 288)
+        return f"gather_window_kernel<{P},{sw},f32,{wb}> + direct_reduce_kernel<{P},1>"
+    return f"gather_direct_kernel<{P},{sw},f32,table> + direct_reduce_kernel<{P},{sw}>"
 
 
 def ncu_traffic(per_update_units):
@@ -836,7 +848,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": peak_kind,
                 "traffic": ncu_traffic(updates),
-                "kernel": "gather_direct_kernel<128,4,f32,table> + direct_reduce_kernel<128,4>",
+                "kernel": single_frame_kernels(info),
                 "timed": "the gather and its reduction (split-call API), by events on the launching stream",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "path_us": statistics.mean(path_ms) * 1e3,

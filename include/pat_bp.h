@@ -78,6 +78,12 @@ typedef void* pat_stream_t; /* a cudaStream_t; NULL = legacy default stream */
                                          pipeline) gather too; by default one
                                          frame takes the unstaged kernel, which
                                          gives the same bits                     */
+#define PAT_FLAG_NO_WINDOW 0x1000u /* unstaged single frames of a stored table
+                                      gather the integrand from L2 instead of
+                                      from shared-memory windows (the default
+                                      whenever every window of the table has at
+                                      most 288 samples); same bits, for
+                                      comparisons                               */
 
 /* Read-only facts about a handle (pat_bp_info). */
 typedef struct {

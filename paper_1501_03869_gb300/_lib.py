@@ -34,6 +34,7 @@ EXPORTS = (
 )
 PAT_FLAG_HOST_MIRROR = 0x100
 PAT_FLAG_STAGED_SINGLE = 0x200
+PAT_FLAG_NO_WINDOW = 0x1000
 PAT_FLAG_FMM_SECOND_ORDER = 0x400
 PAT_FLAG_GPU_TABLE = 0x800
 PAT_PLAN_AUTOTUNE = 0x1

@@ -1,4 +1,11 @@
-// gather_direct.cu -- the single-frame gather of Eq. (BP) without staging.
+// gather_direct.cu -- the single-frame gather of Eq. (BP) without the staged
+// pipeline.
+//
+// Two gathers share the reduction kernel below.  gather_window_kernel (stored
+// tables without weights, every window at most 288 samples) copies each
+// sensor's integrand window into shared memory per warp and interpolates
+// there; gather_direct_kernel, described next, gathers from L2 and takes every
+// other case.  Both give the same bits.
 //
 // Two launches.  The gather kernel is persistent: CTA c takes units (tile,
 // segment of G sensors) c, c + grid, c + 2 grid, ... in tile-major order, and
@@ -56,6 +63,7 @@ struct DirectParams {
   int* host_status;  // the reduction copies *status here when set
   uint64_t timeout_ns;  // bound of every device-side wait
   int n_zero_runs, n_sensors, n_sensors_pad, n_t_pad, n_tiles, n_seg, G;
+  int W;  // longest window of one (tile, sensor) (rows)
 };
 
 // One sensor's contribution to this lane's 4 pixels; `row` points at the
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(32 * (P / 128) * SW, kDirectMinCtas)
 }
 
 // Sum of every pixel over phases (in order) and segments (in order), written
-// to its place in the image; also clears the image outside the mask.  The
+// to its place in the image (SW = 1: the part buffer holds segment sums); also clears the image outside the mask.  The
 // loads of 8 segments are issued before their sums, so a pixel costs about
 // one L2 round trip per 8 segments.
 template <int P, int SW>
@@ -284,13 +292,172 @@ __global__ void __launch_bounds__(256) direct_reduce_kernel(const __grid_constan
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (s0 + k >= p.n_seg) break;
-        float v = 0.0f;
+        if constexpr (SW == 1) {
+          t += x[k][0];  // phases already summed, in the same order, by the gather
+        } else {
+          float v = 0.0f;
 #pragma unroll
-        for (int ph = 0; ph < SW; ++ph) v += x[k][ph];
-        t += v;
+          for (int ph = 0; ph < SW; ++ph) v += x[k][ph];
+          t += v;
+        }
       }
     }
     p.out[o] = t;
+  }
+}
+
+// ------------------------------------------------------ windowed variant --
+// Stored tables without solid-angle weights, when every window of the table
+// fits a shared-memory slot of WB rows.  The four warps of a CTA are the four
+// (pixel group, sensor phase) pairs of one unit, as above; a warp takes its
+// sensors two at a time.  For each sensor it copies the tile's integrand
+// window (rows base .. base + len) into a slot of its own with 16-byte
+// cp.async copies, two steps ahead, while its lanes' table offsets come from
+// global memory one step ahead; the interpolation then reads shared memory.
+// Each slot ends in 8 zero rows at row WB: an offset after the record (the
+// table's out-of-record value) is clamped to WB, which gives phase 0 and the
+// zero rows, so it adds m * 0 as in the kernel above.  The CTA sums its four
+// phase sums per pixel in order before storing, so the reduction kernel sums
+// segments only.  Arithmetic and summation order are those of
+// gather_direct_kernel: the image has the same bits.
+//
+// Offsets in the window are found from the FP32 bits: for 0 <= u < 2^23,
+// u + 2^23 rounded toward zero is 2^23 + floor(u) exactly, its bit pattern is
+// 0x4B000000 + floor(u), and (u + 2^23) - 2^23 = floor(u) exactly.
+constexpr int kWindowMaxRows = 288;  // largest slot (rows); longer windows take the kernel above
+
+template <int P, int SW, int FMT, int WB>
+__global__ void __launch_bounds__(128, kDirectMinCtas + 1)
+    gather_window_kernel(const __grid_constant__ DirectParams p) {
+  constexpr int PW = P / 128;
+  static_assert(PW * SW == 4, "a unit is four warps");
+  constexpr int SLOT = WB + 8;  // rows of one slot: window, then 8 zero rows
+  constexpr int D = 2;          // steps of two sensors whose windows are in flight
+  constexpr int NC = (WB + 127) / 128;  // 16-byte copies per lane for one window
+  __shared__ __align__(16) uint32_t swin[4][2 * D][SLOT];
+  __shared__ __align__(16) uint2 sbm[4][32];  // (window base word, multiplier) per sensor of the warp
+  __shared__ float ssum[SW][P];
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pg = warp % PW, sp = warp / PW;
+  const int px0 = pg * 128 + lane;
+  uint32_t* ring = &swin[warp][0][0];
+  for (int k = lane; k < 2 * D * 8; k += 32) ring[(k >> 3) * SLOT + WB + (k & 7)] = 0u;
+  const uint32_t ring_s = smem_addr(ring);
+  const int64_t n_units = int64_t(p.n_tiles) * p.n_seg;
+  const uint32_t* bsrc = static_cast<const uint32_t*>(p.b);
+  const uint2* bm = sbm[warp];
+  // integrand and multipliers come from the preprocessing grid
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  for (int64_t unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+    const int tile = int(unit / p.n_seg);
+    const int seg = int(unit - int64_t(tile) * p.n_seg);
+    const int s_lo = seg * p.G, s_hi = min(p.n_sensors, s_lo + p.G);
+    const int s0 = s_lo + sp;  // this warp's sensors: s0, s0 + SW, ...
+    const int nj = s0 < s_hi ? (s_hi - s0 + SW - 1) / SW : 0;  // <= 32 (G <= 32 SW)
+    if (lane < nj) {
+      const int s = s0 + lane * SW;
+      sbm[warp][lane] = make_uint2(uint32_t(__ldcg(p.base + int64_t(tile) * p.n_sensors_pad + s)),
+                                   __float_as_uint(__ldcg(p.m + s)));
+    }
+    __syncwarp();
+    const float* ubase = p.u + (int64_t(tile) * p.n_sensors + s0) * P + px0;
+    const uint32_t* wsrc = bsrc + int64_t(s0) * p.n_t_pad + lane * 4;
+    const int64_t ustep = int64_t(SW) * P, wstep = int64_t(SW) * p.n_t_pad;
+    // windows of the sensors 2k, 2k + 1 into slots 2 slot, 2 slot + 1; one group per step
+    auto issue = [&](int k, int slot) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * k + h;
+        if (j < nj) {
+          const uint32_t b = bm[j].x;
+          const int len = int(b >> 16);
+          const uint32_t sa = ring_s + uint32_t(((2 * slot + h) * SLOT + lane * 4) * 4);
+          const uint32_t* src = wsrc + j * wstep + (b & 0xffffu);
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            if (lane * 4 + c * 128 < len) cp_async16(sa + c * 512, src + c * 128);
+        }
+      }
+      cp_async_commit();
+    };
+    // the lanes' offsets of the sensors 2k, 2k + 1
+    auto load_u = [&](int k, float (&d)[2][4]) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float* ur = ubase + min(2 * k + h, nj - 1) * ustep;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) d[h][x] = __ldcg(ur + 32 * x);
+      }
+    };
+    // interpolation of one sensor at the lane's 4 offsets; wadj = the slot's
+    // row 0 minus 4 * 0x4B000000 (shared addresses wrap modulo 2^32)
+    auto lerp4 = [&](uint32_t wadj, const float (&uu)[4], float (&v)[4]) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const float uc = fminf(uu[x], float(WB));
+        const float t = __fadd_rz(uc, 8388608.0f);
+        const float ph = __fsub_rn(uc, __fsub_rn(t, 8388608.0f));
+        const uint32_t a = wadj + 4u * __float_as_uint(t);
+        const uint32_t w0 = lds_u32(a);
+        if constexpr (FMT == kBF32) {
+          const float b0 = __uint_as_float(w0), b1 = __uint_as_float(lds_u32(a + 4));
+          v[x] = fmaf(ph, b1 - b0, b0);
+        } else if constexpr (FMT == kBBF16P) {
+          v[x] = fmaf(ph, __uint_as_float(w0 & 0xffff0000u), __uint_as_float(w0 << 16));
+        } else {
+          const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&w0));
+          v[x] = fmaf(ph, hf.y, hf.x);
+        }
+      }
+    };
+    const int nk = (nj + 1) >> 1;
+    float un[2][4];
+    if (nk > 0) load_u(0, un);
+#pragma unroll
+    for (int k = 0; k < D; ++k) issue(k, k);
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int slot = 0;
+    for (int k = 0; k < nk; ++k) {
+      float uc[2][4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) uc[h][x] = un[h][x];
+      if (k + 1 < nk) load_u(k + 1, un);
+      cp_async_wait<D - 1>();
+      __syncwarp();
+      const int j = 2 * k;
+      const uint4 q = *reinterpret_cast<const uint4*>(bm + j);  // sensors j and j + 1
+      const uint32_t wa = ring_s + uint32_t(2 * slot * SLOT * 4) - 4u * 0x4B000000u;
+      float va[4];
+      lerp4(wa, uc[0], va);
+      if (j + 1 < nj) {
+        float vb[4];
+        lerp4(wa + SLOT * 4, uc[1], vb);
+        const float ma = __uint_as_float(q.y), mb = __uint_as_float(q.w);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) acc[x] = fmaf(mb, vb[x], fmaf(ma, va[x], acc[x]));
+      } else {
+        const float ma = __uint_as_float(q.y);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) acc[x] = fmaf(ma, va[x], acc[x]);
+      }
+      __syncwarp();  // every lane has read the slots before they are refilled
+      issue(k + D, slot);
+      slot ^= 1;
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int x = 0; x < 4; ++x) ssum[sp][px0 + 32 * x] = acc[x];
+    __syncthreads();
+    for (int q = threadIdx.x; q < P; q += 128) {
+      float v = 0.0f;
+#pragma unroll
+      for (int ph = 0; ph < SW; ++ph) v += ssum[ph][q];
+      p.part[(int64_t(tile) * p.n_seg + seg) * P + q] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -341,6 +508,45 @@ cudaError_t launch_direct_fmt(const DirectParams& dp, int n_sm, cudaStream_t st)
   return launch_pdl(direct_reduce_kernel<P, SW>, std::max(rgrid, 1u), 256u, dp, st);
 }
 
+template <int P, int SW, int FMT, int WB>
+cudaError_t launch_window_fmt(const DirectParams& dp, int n_sm, cudaStream_t st) {
+  auto kern = gather_window_kernel<P, SW, FMT, WB>;
+  static PerDevice cache;  // resident CTAs per SM, per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (cache.per_sm[dev] == 0) {
+    int v = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 128, 0);
+    if (e != cudaSuccess) return e;
+    cache.per_sm[dev] = v > 0 ? v : 1;
+  }
+  const int64_t n_units = int64_t(dp.n_tiles) * dp.n_seg;
+  const unsigned grid = unsigned(std::min<int64_t>(n_units, int64_t(cache.per_sm[dev]) * n_sm));
+  e = launch_pdl(kern, grid, 128u, dp, st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = int64_t(dp.n_tiles) * P;
+  const unsigned rgrid = unsigned(std::min<int64_t>((n + 255) / 256, int64_t(n_sm) * 8));
+  return launch_pdl(direct_reduce_kernel<P, 1>, std::max(rgrid, 1u), 256u, dp, st);
+}
+
+template <int P, int SW, int WB>
+cudaError_t launch_window_w(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
+  if (fmt == kBF32) return launch_window_fmt<P, SW, kBF32, WB>(dp, n_sm, st);
+  if (fmt == kBBF16P) return launch_window_fmt<P, SW, kBBF16P, WB>(dp, n_sm, st);
+  if (fmt == kBF16P) return launch_window_fmt<P, SW, kBF16P, WB>(dp, n_sm, st);
+  return cudaErrorInvalidValue;
+}
+
+// The smallest slot (128, 192 or 288 rows) that holds every window.
+template <int P, int SW>
+cudaError_t launch_window(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
+  if (dp.W <= 128) return launch_window_w<P, SW, 128>(fmt, dp, n_sm, st);
+  if (dp.W <= 192) return launch_window_w<P, SW, 192>(fmt, dp, n_sm, st);
+  return launch_window_w<P, SW, kWindowMaxRows>(fmt, dp, n_sm, st);
+}
+
 template <int P, int SW, int DELAYS, int WGT>
 cudaError_t launch_direct_w(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
   if (fmt == kBF32) return launch_direct_fmt<P, SW, kBF32, DELAYS, WGT>(dp, n_sm, st);
@@ -387,6 +593,12 @@ cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc&
   dp.n_tiles = d.n_tiles;
   dp.n_seg = d.n_seg;
   dp.G = d.G;
+  dp.W = d.W;
+  // stored tables without weights: the windowed kernel when every window fits a slot
+  const bool window = !c.delays && !dp.wanchor && !c.no_window && dp.W >= 0 &&
+                      dp.W <= kWindowMaxRows && dp.G <= 32 * c.SW;
+  if (window && c.P == 128 && c.SW == 4) return launch_window<128, 4>(fmt, dp, n_sm, st);
+  if (window && c.P == 256 && c.SW == 2) return launch_window<256, 2>(fmt, dp, n_sm, st);
   if (c.P == 128 && c.SW == 4)
     return c.delays ? launch_direct_t<128, 4, 1>(fmt, dp, n_sm, st)
                     : launch_direct_t<128, 4, 0>(fmt, dp, n_sm, st);

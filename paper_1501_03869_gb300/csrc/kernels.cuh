@@ -63,6 +63,7 @@ struct InstDesc {
   int64_t unit_begin;       // index of this instance's first unit
   int n_zero_runs;
   int n_sensors, n_sensors_pad, n_t_pad, n_tiles, n_frames, n_fg, n_seg, G, Wst;
+  int W;                    // longest window of one (tile, sensor) (rows)
 };
 
 struct StreamParams {
@@ -88,6 +89,7 @@ struct GatherConfig {
   int delays = 0;   // 0 stored table, 1 constant speed computed in the kernel
   int wgt = 0;      // 1: solid-angle weights per (pixel, sensor)
   int direct = 0;   // 1: single frame through the unstaged kernels (gather_direct.cu)
+  int no_window = 0;  // 1: the unstaged kernel gathers from L2, never from shared-memory windows
   int n_sm = 0;     // multiprocessors of the device (sizes the unstaged grid)
 };
 

@@ -487,6 +487,7 @@ GatherConfig pick_config(pat_bp_t h, int n_frames, int fmt, int* wst) {
     // frame on the 3-D subject)
     GatherConfig c = config_for(h, 1, 16, 72 * 1024, wst);
     c.direct = 1;
+    c.no_window = (h->flags & PAT_FLAG_NO_WINDOW) != 0;
     return c;
   }
   for (int FB = frames_per_group(n_frames); FB >= 1; FB /= 2) {
@@ -549,6 +550,7 @@ InstDesc make_desc(pat_bp_t h, float* out, int n_frames, int FB, int wst) {
   d.n_seg = h->n_seg;
   d.G = h->G;
   d.Wst = wst;
+  d.W = h->W;
   return d;
 }
 

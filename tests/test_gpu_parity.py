@@ -140,6 +140,11 @@ def test_ragged_and_degenerate_shapes(ns, nt, F, shape, hole):
         assert rel_l2(got[f], ref[f]) <= FP32_REL_L2
         assert np.abs(got[f] - ref[f]).max() <= FP32_MAX_ABS_FRAC * scale
     assert np.all(got[:, ~mask.astype(bool)] == 0.0)
+    if F <= 3:
+        # frame by frame through the unstaged kernels: the windowed kernel
+        # (default) and the one that gathers from L2 give the same bits
+        alt, _ = gpu_images(w, flags=_lib.PAT_FLAG_NO_WINDOW)
+        assert np.array_equal(got, alt)
 
 
 def test_3d_volume_small():
@@ -265,8 +270,12 @@ def test_single_frame_unstaged_equals_staged_bitwise(tile_flag):
                                           w.nt, mask=w.mask, flags=f | tile_flag),
     }
     for kind, make in makers.items():
-        with make(0) as a, make(_lib.PAT_FLAG_STAGED_SINGLE) as b:
+        with make(0) as a, make(_lib.PAT_FLAG_STAGED_SINGLE) as b, \
+                make(_lib.PAT_FLAG_NO_WINDOW) as c:
             assert a.info["split"] == 8
+            if kind == "table" and tile_flag != _lib.PAT_FLAG_TILE_256:
+                # every window fits a slot: the default takes the windowed kernel
+                assert a.info["window"] <= 288
             for dtype in ("f32", "bf16", "f16"):
                 if dtype == "f32":
                     s = torch.from_numpy(np.ascontiguousarray(sig)).cuda()
@@ -278,9 +287,12 @@ def test_single_frame_unstaged_equals_staged_bitwise(tile_flag):
                     sc = torch.from_numpy(scl).cuda()
                 ra = a.reconstruct(s, scales=sc).cpu().numpy()
                 rb = b.reconstruct(s, scales=sc).cpu().numpy()
+                rc = c.reconstruct(s, scales=sc).cpu().numpy()
                 a.sync()
                 b.sync()
+                c.sync()
                 assert np.array_equal(ra, rb), (kind, dtype)
+                assert np.array_equal(ra, rc), (kind, dtype)
                 assert np.isfinite(ra).all()
 
 
