@@ -277,18 +277,19 @@ __global__ void __launch_bounds__(256) direct_reduce_kernel(const __grid_constan
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n;
        idx += int64_t(gridDim.x) * blockDim.x) {
     const int o = __ldcg(p.slot + idx);
-    if (o < 0) continue;
     const int64_t tile = idx / P;
     const int q = int(idx - tile * P);
     const float* src = p.part + tile * p.n_seg * SW * P + q;
     float t = 0.0f;
     for (int s0 = 0; s0 < p.n_seg; s0 += K) {
+      // (the first batch is loaded together with the slot, before its test)
       float x[K][SW];
 #pragma unroll
       for (int k = 0; k < K; ++k)
 #pragma unroll
         for (int ph = 0; ph < SW; ++ph)
           x[k][ph] = s0 + k < p.n_seg ? __ldcg(src + (int64_t(s0 + k) * SW + ph) * P) : 0.0f;
+      if (o < 0) break;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (s0 + k >= p.n_seg) break;
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(256) direct_reduce_kernel(const __grid_constan
         }
       }
     }
-    p.out[o] = t;
+    if (o >= 0) p.out[o] = t;
   }
 }
 
@@ -355,15 +356,27 @@ __global__ void __launch_bounds__(128, kDirectMinCtas + 1)
     const int s_lo = seg * p.G, s_hi = min(p.n_sensors, s_lo + p.G);
     const int s0 = s_lo + sp;  // this warp's sensors: s0, s0 + SW, ...
     const int nj = s0 < s_hi ? (s_hi - s0 + SW - 1) / SW : 0;  // <= 32 (G <= 32 SW)
+    const float* ubase = p.u + (int64_t(tile) * p.n_sensors + s0) * P + px0;
+    const uint32_t* wsrc = bsrc + int64_t(s0) * p.n_t_pad + lane * 4;
+    const int64_t ustep = int64_t(SW) * P, wstep = int64_t(SW) * p.n_t_pad;
+    // the lanes' offsets of the sensors 2k, 2k + 1
+    auto load_u = [&](int k, float (&d)[2][4]) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float* ur = ubase + min(2 * k + h, nj - 1) * ustep;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) d[h][x] = __ldcg(ur + 32 * x);
+      }
+    };
+    const int nk = (nj + 1) >> 1;
+    float un[2][4];
+    if (nk > 0) load_u(0, un);  // in flight with the window bases below
     if (lane < nj) {
       const int s = s0 + lane * SW;
       sbm[warp][lane] = make_uint2(uint32_t(__ldcg(p.base + int64_t(tile) * p.n_sensors_pad + s)),
                                    __float_as_uint(__ldcg(p.m + s)));
     }
     __syncwarp();
-    const float* ubase = p.u + (int64_t(tile) * p.n_sensors + s0) * P + px0;
-    const uint32_t* wsrc = bsrc + int64_t(s0) * p.n_t_pad + lane * 4;
-    const int64_t ustep = int64_t(SW) * P, wstep = int64_t(SW) * p.n_t_pad;
     // windows of the sensors 2k, 2k + 1 into slots 2 slot, 2 slot + 1; one group per step
     auto issue = [&](int k, int slot) {
 #pragma unroll
@@ -380,15 +393,6 @@ __global__ void __launch_bounds__(128, kDirectMinCtas + 1)
         }
       }
       cp_async_commit();
-    };
-    // the lanes' offsets of the sensors 2k, 2k + 1
-    auto load_u = [&](int k, float (&d)[2][4]) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float* ur = ubase + min(2 * k + h, nj - 1) * ustep;
-#pragma unroll
-        for (int x = 0; x < 4; ++x) d[h][x] = __ldcg(ur + 32 * x);
-      }
     };
     // interpolation of one sensor at the lane's 4 offsets; wadj = the slot's
     // row 0 minus 4 * 0x4B000000 (shared addresses wrap modulo 2^32)
@@ -411,9 +415,6 @@ __global__ void __launch_bounds__(128, kDirectMinCtas + 1)
         }
       }
     };
-    const int nk = (nj + 1) >> 1;
-    float un[2][4];
-    if (nk > 0) load_u(0, un);
 #pragma unroll
     for (int k = 0; k < D; ++k) issue(k, k);
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
