@@ -149,3 +149,40 @@ def test_plan_follows_evict_restore_and_refuses_changed_weights():
     plan.close()
     ha.close()
     hb.close()
+
+
+def test_tile256_tuned_graph_plan_matches_single_handles_and_oracle():
+    """The uneven workload with 256-pixel tiles (the benchmark's form): a tuned,
+    graph-replayed plan over every instance gives each instance the bits of its
+    own single-handle reconstruction; the cheapest instance matches the oracle."""
+    from paper_1501_03869_gb300 import _lib
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ws = [synth.config4_instance(i) for i in range(32)]
+    bps = [BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask,
+              flags=_lib.PAT_FLAG_TILE_256) for w in ws]
+    try:
+        sig = [torch.from_numpy(w.signals).cuda() for w in ws]
+        single = [bp.reconstruct(s).cpu().numpy() for bp, s in zip(bps, sig)]
+        plan = Plan(bps, [w.n_frames for w in ws], autotune=True, graph=True)
+        outs = _outs(bps, ws)
+        plan.execute(sig, outs)
+        plan.sync()
+        assert bps[0].info["tile_pix"] == 256 and plan.info["graph"] == 1
+        for i, o in enumerate(outs):
+            assert np.array_equal(o.cpu().numpy(), single[i]), f"instance {i}"
+        plan.close()
+        i = min(range(32), key=lambda k: ws[k].n_frames * ws[k].n_sensors * ws[k].n_pix)
+        w = ws[i]
+        pix = np.flatnonzero(w.mask.ravel())
+        T = travel_table(f"c4_{i}", w.speed, w.dx, w.origin, w.sensors, pix)
+        ref = oracle.reconstruct(w.speed, w.dx, w.origin, w.sensors, w.signals, w.dt, w.mask, T=T)
+        p0 = np.abs(w.p0).max()
+        for f in range(w.n_frames):
+            got = single[i][f].astype(np.float64).ravel()
+            r = ref[f].ravel()
+            assert np.linalg.norm(got - r) / np.linalg.norm(r) <= FP32_REL_L2
+            assert np.abs(got - r).max() <= FP32_MAX_ABS_FRAC * p0
+    finally:
+        for bp in bps:
+            bp.close()
