@@ -323,6 +323,24 @@ def oracle_leg(w, checks):
                 worst = a
         worst["frames"] = int(wi.n_frames)
         acc[key] = worst
+    if "c3" in checks:
+        # every frame of the precision form against the oracle on the original
+        # FP32 signals (the 5e-3 gate) and on the dequantised input (the kernel's
+        # own arithmetic)
+        w3, imgs = checks["c3"]
+        pix3 = np.flatnonzero(w3.mask.ravel())
+        T3 = oracle.travel_table(w3.speed, w3.dx, w3.origin, w3.sensors, pix3)
+        refs = [oracle.bp(T3, w3.signals[f].astype(np.float64), w3.dt) for f in range(w3.n_frames)]
+        for dtype, img in imgs.items():
+            _, _, deq = synth.quantise(w3.signals, dtype)
+            e = [accuracy(img[f].ravel()[pix3], refs[f], float(np.abs(w3.p0).max()))["rel_l2"]
+                 for f in range(w3.n_frames)]
+            eq = [accuracy(img[f].ravel()[pix3], oracle.bp(T3, deq[f].astype(np.float64), w3.dt),
+                           float(np.abs(w3.p0).max()))["rel_l2"] for f in range(w3.n_frames)]
+            acc[f"precision_c3_{dtype}"] = {"frames": int(w3.n_frames),
+                                            "rel_l2_max": float(max(e)), "rel_l2_mean": float(np.mean(e)),
+                                            "rel_l2_vs_dequantised_max": float(max(eq)),
+                                            "gate": 5e-3}
     out["accuracy_vs_oracle"] = acc
     return out
 
@@ -660,6 +678,93 @@ def time_steps_warm(fn, steps, warmup):
     return recs
 
 
+def c3_form(args, flush, stream, checks):
+    """The precision form: the 128x128 geometry (64 sensors, 1024 samples, 6 092
+    pixels), 64 frames sharing one table, BF16 and FP16 signals with per-row
+    FP32 scales, FP32 accumulation; each batch is the whole user call
+    (preprocessing + gather) replayed as a CUDA graph, L2 flushed before it.
+    The per-frame error against the FP64 oracle is added in the host leg."""
+    import torch
+    from paper_1501_03869_gb300 import BP, synth
+    Ev = torch.cuda.Event
+    w = synth.config3(n_frames=64)
+    bp = BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask)
+    res = {"workload": "128x128 at 0.2 mm, 64 sensors, 1024 samples, 6092-pixel mask, 64 frames, "
+                       "16-bit signals with per-row FP32 scales", "frames": 64}
+    imgs = {}
+    for dtype, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        codes, sc, _ = synth.quantise(w.signals, dtype)
+        s16 = torch.from_numpy(codes.astype(np.int16)).cuda().view(tdt)
+        scl = torch.from_numpy(sc).cuda()
+        out = torch.empty(bp.out_shape(64), device="cuda")
+        bp.autotune(s16, scales=scl, out=out)
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            bp.reconstruct(s16, scales=scl, out=out, stream=side)
+        stream.wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            bp.reconstruct(s16, scales=scl, out=out, stream=torch.cuda.current_stream())
+
+        def step():
+            e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            return e0, e1
+
+        n = max(20, min(args.steps // 10, 200))
+        ms = statistics.mean(a.elapsed_time(b) for a, b in time_steps(step, n, args.warmup, stream, flush))
+        upd = 64 * int(w.n_pix) * w.n_sensors
+        res[dtype] = {"ms_per_batch": ms, "frames_per_s": 64 / (ms / 1e3),
+                      "value": upd / (ms / 1e3) / 1e9, "unit": UNIT}
+        imgs[dtype] = out.cpu().numpy()
+    bp.close()
+    checks["c3"] = (w, imgs)
+    return res
+
+
+def c5_frame_form(args, flush, stream):
+    """One full-size 3-D frame (160x160x96 at 0.25 mm, every voxel, 1024 sensors,
+    a 10 GB GPU-solved table), FP32 and BF16 signals: the whole user call by
+    events, L2 flushed before it, with its HBM roofline (table + signals +
+    image bytes over the call time)."""
+    import torch
+    from paper_1501_03869_gb300 import BP, _lib, synth
+    Ev = torch.cuda.Event
+    w = synth.config5_subject(0, n_frames=1)
+    bp = BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask, flags=_lib.PAT_FLAG_GPU_TABLE)
+    codes, sc, _ = synth.quantise(w.signals, "bf16")
+    inputs = {"f32": (torch.from_numpy(w.signals).cuda(), None, 4),
+              "bf16": (torch.from_numpy(codes.astype(np.int16)).cuda().view(torch.bfloat16),
+                       torch.from_numpy(sc).cuda(), 2)}
+    hbm_peak, kind = peaks()
+    upd = int(w.n_pix) * w.n_sensors
+    res = {"workload": "160x160x96 at 0.25 mm, 2 457 600 voxels, 1024 hemisphere sensors, 2048 samples, "
+                       "GPU-solved table", "table_gb": bp.info["table_bytes"] / 1e9,
+           "window": bp.info["window"]}
+    for dt, (sig, scl, esz) in inputs.items():
+        out = torch.empty(bp.out_shape(1), device="cuda")
+
+        def step():
+            e0, e1 = Ev(enable_timing=True), Ev(enable_timing=True)
+            e0.record(stream)
+            bp.reconstruct(sig, scales=scl, out=out, stream=stream)
+            e1.record(stream)
+            return e0, e1
+
+        ms = statistics.median(a.elapsed_time(b) for a, b in time_steps(step, 30, args.warmup, stream, flush))
+        alg = bp.info["table_bytes"] + esz * w.n_sensors * w.nt + 4.0 * w.n_pix
+        res[dt] = {"ms_per_frame": ms, "value": upd / (ms / 1e3) / 1e9, "unit": UNIT,
+                   "roofline": {"bound": "hbm", "algorithmic_bytes": alg,
+                                "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                "frac": alg / (ms / 1e3) / 1e9 / hbm_peak, "peak_source": kind,
+                                "timed": "the whole call (preprocessing, gather, reduction) by events"}}
+    bp.close()
+    return res
+
+
 def c1_form(args, flush, stream, checks):
     """Latency of the small single-frame workload (128x128 grid, 64 sensors,
     1024 samples, 6 092 pixels): the user call replayed as a CUDA graph, L2
@@ -891,6 +996,8 @@ def main():
                                    "unit": UNIT, "frames_per_s": 1e3 / warm_ms}
     if not args.no_forms:
         forms["latency_c1"] = c1_form(args, flush, stream, checks)
+        forms["precision_c3"] = c3_form(args, flush, stream, checks)
+        forms["single_frame_c5"] = c5_frame_form(args, flush, stream)
     if not args.no_forms and args.batch_frames > 1:
         F = args.batch_frames
         from paper_1501_03869_gb300 import _lib
