@@ -898,12 +898,26 @@ def main():
         e2.record(stream)
         return e0, e1, e2
 
+    def gather_only():
+        # the gather kernel alone (measurement hook: no reduction into the image)
+        import ctypes
+        e0, e1, e2 = Ev(enable_timing=True), Ev(enable_timing=True), Ev(enable_timing=True)
+        e0.record(stream)
+        bp.preprocess(sig, stream=stream)
+        e1.record(stream)
+        rc = bp._lib.pat_test_gather_only(bp._h, ctypes.c_void_p(stream.cuda_stream))
+        e2.record(stream)
+        if rc != 0:
+            raise RuntimeError(f"pat_test_gather_only: status {rc}")
+        return e0, e1, e2
+
     # per-kernel device times (events on the launching stream, L2 flushed)
     n_k = max(20, min(args.steps, 200))
     path_ms = [a.elapsed_time(b) for a, b in time_steps(path_kernels, n_k, args.warmup, stream, flush)]
     kr = time_steps(split_kernels, n_k, args.warmup, stream, flush)
     pre_ms = [a.elapsed_time(b) for a, b, c in kr]
     gat_ms = [b.elapsed_time(c) for a, b, c in kr]
+    go_ms = [b.elapsed_time(c) for a, b, c in time_steps(gather_only, n_k, args.warmup, stream, flush)]
 
     # one step = the on-line path (the user call) captured once as a CUDA graph, replayed
     side = torch.cuda.Stream()
@@ -950,17 +964,27 @@ def main():
 
     # ------------------------------------------------------------ roofline --
     hbm_peak, peak_kind = peaks()
-    alg_bytes = 4.0 * ns * n_pix + 4.0 * ns * nt + 4.0 * n_pix
+    # the gather kernel reads the table and the integrand; its reduction reads
+    # the segment sums and writes the image (4 bytes per pixel)
+    alg_bytes = 4.0 * ns * n_pix + 4.0 * ns * nt
+    alg_bytes_red = alg_bytes + 4.0 * n_pix
+    go_avg_s = statistics.mean(go_ms) / 1e3
+    achieved = alg_bytes / go_avg_s / 1e9
     gat_avg_s = statistics.mean(gat_ms) / 1e3
-    achieved = alg_bytes / gat_avg_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": peak_kind,
                 "traffic": ncu_traffic(updates),
-                "kernel": single_frame_kernels(info),
-                "timed": "the gather and its reduction (split-call API), by events on the launching stream",
+                "kernel": single_frame_kernels(info).split(" + ")[0],
+                "timed": "the gather kernel alone (pat_test_gather_only after the preprocessing), by events "
+                         "on the launching stream, L2 flushed before every step",
                 "algorithmic_bytes_per_launch": alg_bytes,
+                "with_reduction": {"kernels": single_frame_kernels(info),
+                                   "timed": "the gather and its reduction (split-call API), by events",
+                                   "us": gat_avg_s * 1e6, "algorithmic_bytes": alg_bytes_red,
+                                   "frac": alg_bytes_red / gat_avg_s / 1e9 / hbm_peak},
                 "path_us": statistics.mean(path_ms) * 1e3,
                 "split_call_us": {"preprocess": statistics.mean(pre_ms) * 1e3,
+                                  "gather_alone": statistics.mean(go_ms) * 1e3,
                                   "gather_and_reduction": statistics.mean(gat_ms) * 1e3}}
 
     # ------------------------------------------------------------------ e2e --

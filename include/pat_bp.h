@@ -448,6 +448,16 @@ pat_status pat_probe_l2_to_smem(double* gbps);
  * failure path of every bounded device wait without faulting the GPU. */
 pat_status pat_test_wait_timeout(uint64_t timeout_ns);
 
+/* pat_test_gather_only -- measurement hook, no counterpart in the paper: after
+ * pat_bp_preprocess of one frame, launches the single-frame gather kernel of
+ * pat_bp_gather alone on `stream` (asynchronous), without the reduction that
+ * sums its per-segment results into the image, so that the gather kernel's own
+ * duration can be timed with events around this call.  The image is not
+ * written; a following pat_bp_gather recomputes everything.  Errors:
+ * PAT_ERR_INVALID (NULL handle, no one-frame preprocess before, or a handle
+ * whose single frame takes the staged kernel), PAT_ERR_CUDA. */
+pat_status pat_test_gather_only(pat_bp_t h, pat_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTS = (
     "pat_bp_preprocess", "pat_bp_gather",
     "pat_bp_reconstruct_host", "pat_bp_reserve", "pat_bp_sync", "pat_bp_info",
     "pat_bp_table", "pat_bp_destroy", "pat_fmm_host", "pat_fmm_gpu", "pat_table_host", "pat_bp_set_solid_angle",
-    "pat_test_wait_timeout", "pat_plan_create", "pat_plan_execute", "pat_plan_sync",
+    "pat_test_wait_timeout", "pat_test_gather_only", "pat_plan_create", "pat_plan_execute", "pat_plan_sync",
     "pat_plan_info", "pat_plan_destroy", "pat_bp_reconstruct_multi", "pat_bp_autotune",
     "pat_bp_evict", "pat_bp_restore", "pat_srv_create", "pat_srv_register", "pat_srv_submit",
     "pat_srv_poll", "pat_srv_stats", "pat_srv_destroy", "pat_bp_reconstruct_noalloc",
@@ -181,6 +181,8 @@ def load():
         lib.pat_probe_l2_to_smem.argtypes = [ctypes.POINTER(ctypes.c_double)]
         lib.pat_test_wait_timeout.restype = _i
         lib.pat_test_wait_timeout.argtypes = [_u64]
+        lib.pat_test_gather_only.restype = _i
+        lib.pat_test_gather_only.argtypes = [_vp, _vp]
         _lib = lib
         return lib
 

@@ -486,7 +486,7 @@ struct PerDevice {
 };
 
 template <int P, int SW, int FMT, int DELAYS, int WGT>
-cudaError_t launch_direct_fmt(const DirectParams& dp, int n_sm, cudaStream_t st) {
+cudaError_t launch_direct_fmt(const DirectParams& dp, int n_sm, cudaStream_t st, bool reduce) {
   auto kern = gather_direct_kernel<P, SW, FMT, DELAYS, WGT>;
   const int threads = 32 * (P / 128) * SW;
   static PerDevice cache;  // resident CTAs per SM, per device
@@ -503,14 +503,14 @@ cudaError_t launch_direct_fmt(const DirectParams& dp, int n_sm, cudaStream_t st)
   const int64_t n_units = int64_t(dp.n_tiles) * dp.n_seg;
   const unsigned grid = unsigned(std::min<int64_t>(n_units, int64_t(cache.per_sm[dev]) * n_sm));
   e = launch_pdl(kern, grid, unsigned(threads), dp, st);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !reduce) return e;
   const int64_t n = int64_t(dp.n_tiles) * P;
   const unsigned rgrid = unsigned(std::min<int64_t>((n + 255) / 256, int64_t(n_sm) * 8));
   return launch_pdl(direct_reduce_kernel<P, SW>, std::max(rgrid, 1u), 256u, dp, st);
 }
 
 template <int P, int SW, int FMT, int WB>
-cudaError_t launch_window_fmt(const DirectParams& dp, int n_sm, cudaStream_t st) {
+cudaError_t launch_window_fmt(const DirectParams& dp, int n_sm, cudaStream_t st, bool reduce) {
   auto kern = gather_window_kernel<P, SW, FMT, WB>;
   static PerDevice cache;  // resident CTAs per SM, per device
   int dev = 0;
@@ -526,40 +526,40 @@ cudaError_t launch_window_fmt(const DirectParams& dp, int n_sm, cudaStream_t st)
   const int64_t n_units = int64_t(dp.n_tiles) * dp.n_seg;
   const unsigned grid = unsigned(std::min<int64_t>(n_units, int64_t(cache.per_sm[dev]) * n_sm));
   e = launch_pdl(kern, grid, 128u, dp, st);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !reduce) return e;
   const int64_t n = int64_t(dp.n_tiles) * P;
   const unsigned rgrid = unsigned(std::min<int64_t>((n + 255) / 256, int64_t(n_sm) * 8));
   return launch_pdl(direct_reduce_kernel<P, 1>, std::max(rgrid, 1u), 256u, dp, st);
 }
 
 template <int P, int SW, int WB>
-cudaError_t launch_window_w(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
-  if (fmt == kBF32) return launch_window_fmt<P, SW, kBF32, WB>(dp, n_sm, st);
-  if (fmt == kBBF16P) return launch_window_fmt<P, SW, kBBF16P, WB>(dp, n_sm, st);
-  if (fmt == kBF16P) return launch_window_fmt<P, SW, kBF16P, WB>(dp, n_sm, st);
+cudaError_t launch_window_w(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st, bool reduce) {
+  if (fmt == kBF32) return launch_window_fmt<P, SW, kBF32, WB>(dp, n_sm, st, reduce);
+  if (fmt == kBBF16P) return launch_window_fmt<P, SW, kBBF16P, WB>(dp, n_sm, st, reduce);
+  if (fmt == kBF16P) return launch_window_fmt<P, SW, kBF16P, WB>(dp, n_sm, st, reduce);
   return cudaErrorInvalidValue;
 }
 
 // The smallest slot (128, 192 or 288 rows) that holds every window.
 template <int P, int SW>
-cudaError_t launch_window(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
-  if (dp.W <= 128) return launch_window_w<P, SW, 128>(fmt, dp, n_sm, st);
-  if (dp.W <= 192) return launch_window_w<P, SW, 192>(fmt, dp, n_sm, st);
-  return launch_window_w<P, SW, kWindowMaxRows>(fmt, dp, n_sm, st);
+cudaError_t launch_window(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st, bool reduce) {
+  if (dp.W <= 128) return launch_window_w<P, SW, 128>(fmt, dp, n_sm, st, reduce);
+  if (dp.W <= 192) return launch_window_w<P, SW, 192>(fmt, dp, n_sm, st, reduce);
+  return launch_window_w<P, SW, kWindowMaxRows>(fmt, dp, n_sm, st, reduce);
 }
 
 template <int P, int SW, int DELAYS, int WGT>
-cudaError_t launch_direct_w(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
-  if (fmt == kBF32) return launch_direct_fmt<P, SW, kBF32, DELAYS, WGT>(dp, n_sm, st);
-  if (fmt == kBBF16P) return launch_direct_fmt<P, SW, kBBF16P, DELAYS, WGT>(dp, n_sm, st);
-  if (fmt == kBF16P) return launch_direct_fmt<P, SW, kBF16P, DELAYS, WGT>(dp, n_sm, st);
+cudaError_t launch_direct_w(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st, bool reduce) {
+  if (fmt == kBF32) return launch_direct_fmt<P, SW, kBF32, DELAYS, WGT>(dp, n_sm, st, reduce);
+  if (fmt == kBBF16P) return launch_direct_fmt<P, SW, kBBF16P, DELAYS, WGT>(dp, n_sm, st, reduce);
+  if (fmt == kBF16P) return launch_direct_fmt<P, SW, kBF16P, DELAYS, WGT>(dp, n_sm, st, reduce);
   return cudaErrorInvalidValue;
 }
 
 template <int P, int SW, int DELAYS>
-cudaError_t launch_direct_t(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st) {
-  return dp.wanchor ? launch_direct_w<P, SW, DELAYS, 1>(fmt, dp, n_sm, st)
-                    : launch_direct_w<P, SW, DELAYS, 0>(fmt, dp, n_sm, st);
+cudaError_t launch_direct_t(int fmt, const DirectParams& dp, int n_sm, cudaStream_t st, bool reduce) {
+  return dp.wanchor ? launch_direct_w<P, SW, DELAYS, 1>(fmt, dp, n_sm, st, reduce)
+                    : launch_direct_w<P, SW, DELAYS, 0>(fmt, dp, n_sm, st, reduce);
 }
 
 }  // namespace
@@ -570,7 +570,7 @@ size_t direct_part_floats(const GatherConfig& c, int n_tiles, int n_seg) {
 
 cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc& d, int n_sm,
                                  int* status, int* host_status, uint64_t timeout_ns,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, bool reduce) {
   if (d.n_frames != 1 || c.FB != 1 || d.n_fg != 1 || n_sm < 1 || !d.part) return cudaErrorInvalidValue;
   DirectParams dp;
   dp.u = d.u;
@@ -598,14 +598,14 @@ cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc&
   // stored tables without weights: the windowed kernel when every window fits a slot
   const bool window = !c.delays && !dp.wanchor && !c.no_window && dp.W >= 0 &&
                       dp.W <= kWindowMaxRows && dp.G <= 32 * c.SW;
-  if (window && c.P == 128 && c.SW == 4) return launch_window<128, 4>(fmt, dp, n_sm, st);
-  if (window && c.P == 256 && c.SW == 2) return launch_window<256, 2>(fmt, dp, n_sm, st);
+  if (window && c.P == 128 && c.SW == 4) return launch_window<128, 4>(fmt, dp, n_sm, st, reduce);
+  if (window && c.P == 256 && c.SW == 2) return launch_window<256, 2>(fmt, dp, n_sm, st, reduce);
   if (c.P == 128 && c.SW == 4)
-    return c.delays ? launch_direct_t<128, 4, 1>(fmt, dp, n_sm, st)
-                    : launch_direct_t<128, 4, 0>(fmt, dp, n_sm, st);
+    return c.delays ? launch_direct_t<128, 4, 1>(fmt, dp, n_sm, st, reduce)
+                    : launch_direct_t<128, 4, 0>(fmt, dp, n_sm, st, reduce);
   if (c.P == 256 && c.SW == 2)
-    return c.delays ? launch_direct_t<256, 2, 1>(fmt, dp, n_sm, st)
-                    : launch_direct_t<256, 2, 0>(fmt, dp, n_sm, st);
+    return c.delays ? launch_direct_t<256, 2, 1>(fmt, dp, n_sm, st, reduce)
+                    : launch_direct_t<256, 2, 0>(fmt, dp, n_sm, st, reduce);
   return cudaErrorInvalidValue;
 }
 

@@ -112,9 +112,11 @@ cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t st)
 // One frame of one instance through the unstaged gather and its reduction
 // kernel (c.FB == 1; d.part holds direct_part_floats floats); same arithmetic
 // and summation order as the staged kernel with one frame per unit.
+// reduce = false launches the gather kernel only (its phase or segment sums;
+// the image is not written): a measurement hook.
 cudaError_t launch_gather_direct(const GatherConfig& c, int fmt, const InstDesc& d, int n_sm,
                                  int* status, int* host_status, uint64_t timeout_ns,
-                                 cudaStream_t st);
+                                 cudaStream_t st, bool reduce = true);
 // Phase sums the unstaged gather stores (floats).
 size_t direct_part_floats(const GatherConfig& c, int n_tiles, int n_seg);
 

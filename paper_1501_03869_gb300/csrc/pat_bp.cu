@@ -1035,6 +1035,21 @@ extern "C" pat_status pat_table_host(const float* speed_host, const pat_grid* gr
   return PAT_OK;
 }
 
+extern "C" pat_status pat_test_gather_only(pat_bp_t h, pat_stream_t stream) {
+  if (!h) return fail(PAT_ERR_INVALID, "NULL handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  PAT_CUDA(cudaSetDevice(h->device));
+  if (h->pre_frames != 1) return fail(PAT_ERR_INVALID, "needs the preprocess of one frame first");
+  int wst = 0;
+  const GatherConfig c = pick_config(h, 1, h->pre_fmt, &wst);
+  if (!c.direct || c.FB != h->pre_fb) return fail(PAT_ERR_INVALID, "the frame does not take the unstaged gather");
+  const InstDesc d = make_desc(h, nullptr, 1, 1, wst);
+  cudaError_t e = launch_gather_direct(c, h->pre_fmt, d, h->n_sm, h->d_status, nullptr, 2000000000ull,
+                                       static_cast<cudaStream_t>(stream), false);
+  if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+  return PAT_OK;
+}
+
 extern "C" pat_status pat_test_wait_timeout(uint64_t timeout_ns) {
   int* d = nullptr;
   PAT_CUDA(cudaMalloc(&d, sizeof(int)));

@@ -332,3 +332,25 @@ def test_second_order_table_fp32_parity():
     assert_fp32_parity(got, ref, np.abs(w.p0).max())
     first, _ = gpu_images(w)
     assert not np.array_equal(first, got)
+
+
+def test_gather_only_hook():
+    """pat_test_gather_only (the benchmark's hook for timing the gather kernel
+    alone) refuses a handle without a one-frame preprocess, leaves the image
+    alone, and a following gather gives the bits of the whole call."""
+    import ctypes
+    w = synth.config2(n_frames=1, n_lines=2)
+    with BP(w.speed, w.dx, w.origin, w.sensors, w.dt, w.nt, mask=w.mask) as bp:
+        st = torch.cuda.current_stream()
+        sp = ctypes.c_void_p(st.cuda_stream)
+        assert bp._lib.pat_test_gather_only(bp._h, sp) == _lib.PAT_ERR_INVALID
+        sig = torch.from_numpy(w.signals).cuda()
+        ref = bp.reconstruct(sig).cpu().numpy()
+        out = torch.full(bp.out_shape(1), 7.0, device="cuda")
+        bp.preprocess(sig)
+        assert bp._lib.pat_test_gather_only(bp._h, sp) == 0
+        bp.sync()
+        assert bool((out == 7.0).all())
+        bp.gather(1, out)
+        bp.sync()
+        assert np.array_equal(out.cpu().numpy(), ref)
