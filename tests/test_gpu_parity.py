@@ -354,3 +354,29 @@ def test_gather_only_hook():
         bp.gather(1, out)
         bp.sync()
         assert np.array_equal(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("dt_ns,wmin,wmax", [(40, 1, 128), (25, 129, 192), (18, 193, 288), (12, 289, 4096)])
+def test_window_slot_sizes_against_l2_staged_and_oracle(dt_ns, wmin, wmax):
+    """The 128^2 geometry sampled at 40, 25, 18 and 12 ns: the table's longest
+    window (the largest one tile needs from one sensor) falls in each slot size
+    of the windowed single-frame gather (128, 192, 288 rows) and beyond it (the
+    L2 gather then runs).  The default path, the L2 gather (PAT_FLAG_NO_WINDOW)
+    and the staged kernel give the same bits; the image matches the oracle."""
+    w1 = synth.config1(n_frames=1)
+    dt = dt_ns * 1e-9
+    nt = int(round(w1.nt * w1.dt / dt))
+    rng = np.random.default_rng(dt_ns)
+    t = np.arange(nt) * dt
+    sig = (np.sin(t[None, None, :] * rng.uniform(2e6, 6e6, (1, w1.n_sensors, 1)) +
+                  rng.uniform(0, 6, (1, w1.n_sensors, 1))) +
+           0.1 * rng.standard_normal((1, w1.n_sensors, nt))).astype(np.float32)
+    w = synth.Workload("slots", w1.speed, w1.dx, w1.origin, w1.sensors, w1.mask, dt, nt, sig, w1.p0)
+    imgs = {}
+    for name, fl in (("default", 0), ("l2", _lib.PAT_FLAG_NO_WINDOW), ("staged", _lib.PAT_FLAG_STAGED_SINGLE)):
+        imgs[name], info = gpu_images(w, flags=fl)
+        assert wmin <= info["window"] <= wmax, info["window"]
+    assert np.array_equal(imgs["default"], imgs["l2"])
+    assert np.array_equal(imgs["default"], imgs["staged"])
+    ref = oracle_images(w, "c1")
+    assert_fp32_parity(imgs["default"], ref, np.abs(ref).max())
