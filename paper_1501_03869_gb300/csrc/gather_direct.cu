@@ -357,6 +357,14 @@ __global__ void __launch_bounds__(128, kDirectMinCtas + 1)
     const int s0 = s_lo + sp;  // this warp's sensors: s0, s0 + SW, ...
     const int nj = s0 < s_hi ? (s_hi - s0 + SW - 1) / SW : 0;  // <= 32 (G <= 32 SW)
     const float* ubase = p.u + (int64_t(tile) * p.n_sensors + s0) * P + px0;
+    if (unit != int64_t(blockIdx.x) && threadIdx.x == 0) {
+      // a CTA's later units (launches with more units than resident CTAs)
+      // start at staggered times: their table block is asked into L2 at once.
+      // (Not the first unit: every CTA asking for its block at the launch's
+      // start delayed the first offsets behind the whole table.)
+      const int n_sen = s_hi - s_lo;
+      bulk_prefetch_l2(p.u + (int64_t(tile) * p.n_sensors + s_lo) * P, uint32_t(n_sen) * P * 4);
+    }
     const uint32_t* wsrc = bsrc + int64_t(s0) * p.n_t_pad + lane * 4;
     const int64_t ustep = int64_t(SW) * P, wstep = int64_t(SW) * p.n_t_pad;
     // the lanes' offsets of the sensors 2k, 2k + 1
